@@ -1,0 +1,87 @@
+"""Pins of the oracle's LIM step (Sec. 3.1, Fig. 1) by properties the method must have:
+p = 1 is explicit Euler; every iteration has the implicit-Euler solution of Eq. (EBlin) as
+its fixed point, so modes at the nodes a_m come out exactly implicit Euler; the step is
+stable on [0, lambda_max]; the scheme has order 1."""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from _dense import dense_Ahat, dense_ghat
+from paper_2502_14589_gb300 import inputs
+
+
+def nodes(p, lmax):
+    """a_m of Fig. 1 steps 2-5 (natural order)."""
+    beta = np.cos(np.pi * (2 * np.arange(1, p + 1) - 1) / (2 * p))
+    z1 = beta[0]
+    return lmax / (1 + z1) * (z1 - beta)
+
+
+def test_p1_is_explicit_euler(oracle):
+    rng = np.random.default_rng(0)
+    N = 20
+    M = rng.standard_normal((N, N)); M = M @ M.T
+    lmax = np.abs(M).sum(axis=0).max()
+    tau = 0.9 / lmax
+    g = rng.standard_normal(N); y = rng.standard_normal(N)
+    out, p = oracle.lim_dense(M, g, y, tau, lmax)
+    assert p == 1
+    np.testing.assert_allclose(out, y + tau * (g - M @ y), rtol=0, atol=1e-14 * np.abs(y).max())
+
+
+@pytest.mark.parametrize("taulam", [3.0, 40.0, 900.0, 2.5e4])
+def test_modes_at_nodes_are_implicit_euler(oracle, taulam):
+    lmax = 1.0e3
+    tau = taulam / lmax
+    p = oracle.cheb_order(tau, lmax)
+    a = nodes(p, lmax)
+    lam = np.concatenate([a, [0.0]])
+    rng = np.random.default_rng(1)
+    g = rng.standard_normal(lam.size); y = rng.standard_normal(lam.size)
+    out, p2 = oracle.lim_dense(np.diag(lam), g, y, tau, lmax)
+    assert p2 == p
+    ie = (y + tau * g) / (1 + tau * lam)          # implicit Euler, Eq. (EBlin)
+    np.testing.assert_allclose(out, ie, rtol=1e-12, atol=1e-12 * np.abs(ie).max())
+
+
+@pytest.mark.parametrize("taulam", [2.0, 50.0, 1e3, 1e5])
+def test_stability_on_zero_to_lambda_max(oracle, taulam):
+    lmax = 10.0
+    tau = taulam / lmax
+    lam = np.linspace(0.0, lmax, 2001)
+    out, p = oracle.lim_dense(np.diag(lam), np.zeros(lam.size), np.ones(lam.size), tau, lmax)
+    assert np.all(np.abs(out) <= 1.0 + 1e-12), (p, np.abs(out).max())
+    assert abs(out[0] - 1.0) < 1e-14                # lambda = 0 mode is kept
+
+
+def test_order_one_on_dense_ch_jacobian(oracle):
+    """Local error against the exact linear solution of Eq. (IVPlin) is O(tau^2)."""
+    n = (6, 6); eps = 0.08
+    y = inputs.initial_state(n, 4, -0.7, 0.7)
+    M = dense_Ahat(n, y, eps); g = dense_ghat(n, y)
+    lmax = np.abs(M).sum(axis=0).max()
+    errs = []
+    for tau in [0.4 / lmax * 2 ** -k for k in range(3)]:
+        N = M.shape[0]
+        aug = np.zeros((N + 1, N + 1)); aug[:N, :N] = -tau * M; aug[:N, N] = tau * (g - M @ y)
+        exact = y + scipy.linalg.expm(aug)[:N, N]
+        out, p = oracle.lim_dense(M, g, y, tau, lmax)
+        errs.append(np.linalg.norm(out - exact))
+    r = [errs[k] / errs[k + 1] for k in range(2)]
+    assert all(3.5 < x < 4.5 for x in r), r
+
+
+def test_grid_lim_matches_dense_lim(oracle):
+    """or_lim_step on the grid = the LIM core on the dense A_hat, g_hat, ||A_hat||_1."""
+    n = (7, 6); eps = 0.06
+    for eyre in (False, True):
+        gr = oracle.Grid(2, n, eps, eyre=eyre)
+        y = inputs.initial_state(n, 9, -0.9, 0.9)
+        M = dense_Ahat(n, y, eps, eyre); gv = dense_ghat(n, y, eyre)
+        lmax = np.abs(M).sum(axis=0).max()
+        tau = 37.0 / lmax
+        out, p, lm, mv = oracle.lim_step(gr, y, tau)
+        ref, p2 = oracle.lim_dense(M, gv, y, tau, lmax)
+        assert p == p2 and mv == 2 * p - 1
+        assert abs(lm - lmax) < 1e-13 * lmax
+        np.testing.assert_allclose(out, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
