@@ -21,6 +21,7 @@
  *    the admissible end;
  *  - constant-step EE2 uses linear residual-time restarting over the whole step with
  *    A_hat, g_hat frozen at y^n;
+ *  - the order of beta_2..beta_p (Fig. 1 step 2) bounds round-off growth (or_lim_order);
  *  - beta == 0 gives y^{n+1} = y^n; est == 0 keeps tau (LIM) or takes 5/4 tau (EE2);
  *  - a step clipped to end at T sets t := T exactly.
  */
@@ -205,23 +206,61 @@ static void dense_matvec(void *ctx, const double *v, double *w) {
     }
 }
 
+/* Fig. 1 step 2 asks for an ORDERED set {beta_m} and fixes only beta_1 = cos(pi/2p) (so
+ * that a_1 = 0 comes first).  Every LIM iteration maps the error against the implicit-
+ * Euler solution of Eq. (EBlin) by the factor (tau a_m - tau A_hat)/(1 + tau a_m); these
+ * factors commute, so the order of beta_2..beta_p does not change the step in exact
+ * arithmetic, only how far the intermediate iterates grow and how much later factors
+ * amplify the rounding errors made on them.  In the natural order i = 2..p the iterates
+ * grow by 1e10 at tau*lambda_max = 700 (1e63 at 2.5e4), which makes the step useless in
+ * FP64 on fine grids.  The order used here is the recursive mirror-pair ordering of
+ * Lebedev and Finogenov (USSR Comput. Math. Math. Phys. 11(2), 1971) for Chebyshev
+ * iteration parameters, extended to odd p:
+ *   order(1) = (1);
+ *   order(p), m = floor(p/2): for each j of order(m) in turn, the pair (j, p + 1 - j);
+ *   for odd p the middle index m + 1 is inserted right after the first pair.
+ * It starts with m = 1, as Fig. 1 requires, and keeps the growth of iterates times the
+ * amplification of later factors near (tau*lambda_max)^2.  The second sweep (steps 9-12)
+ * reuses the order without m = 1.  order[] receives 0-based m.                          */
+#define OR_LIM_MAX_P 1000000
+static void lim_order_rec(int p, int *out) {               /* 1-based, length p */
+    if (p == 1) { out[0] = 1; return; }
+    int m = p / 2, k = 0;
+    int *inner = malloc(m * sizeof(int));
+    lim_order_rec(m, inner);
+    for (int i = 0; i < m; ++i) {
+        out[k++] = inner[i];
+        out[k++] = p + 1 - inner[i];
+        if (i == 0 && (p % 2) == 1) out[k++] = m + 1;
+    }
+    free(inner);
+}
+
+int or_lim_order(int p, int *order) {
+    if (p < 1 || p > OR_LIM_MAX_P) return -1;
+    lim_order_rec(p, order);
+    for (int i = 0; i < p; ++i) order[i] -= 1;
+    return 0;
+}
+
 /* Fig. 1 steps 2-13: one LIM step for y' = -A_hat y + g_hat, y(0) = y^n, with a given
- * spectral bound lambda_max.  Returns p.  Natural order of the beta_m (i = 1..p), and
- * the second sweep reuses a_2..a_p.                                                   */
+ * spectral bound lambda_max.  Returns p (or -1 when p exceeds OR_LIM_MAX_P).           */
 static int lim_core(or_matvec_fn mv, void *ctx, long N, const double *ghat,
                     const double *yn, double tau, double lambda_max, double *ynext,
                     long *matvecs) {
     const double pi = 3.14159265358979323846;
     int p = or_cheb_order(tau, lambda_max);                        /* step 1 */
+    int *order = malloc(p * sizeof(int));
+    if (or_lim_order(p, order) != 0) { free(order); return -1; }   /* step 2 */
     double *beta = malloc(p * sizeof(double)), *a = malloc(p * sizeof(double));
-    for (int i = 1; i <= p; ++i) beta[i - 1] = cos(pi * (2.0 * i - 1.0) / (2.0 * p)); /* 2 */
+    for (int i = 1; i <= p; ++i) beta[i - 1] = cos(pi * (2.0 * i - 1.0) / (2.0 * p));
     double z1 = beta[0];                                           /* step 3 */
     for (int m = 1; m <= p; ++m) a[m - 1] = lambda_max / (1.0 + z1) * (z1 - beta[m - 1]); /* 5 */
     double *prev = malloc(N * sizeof(double)), *Ay = malloc(N * sizeof(double));
     memcpy(prev, yn, N * sizeof(double));                          /* step 3 */
     for (int sweep = 0; sweep < 2; ++sweep) {                      /* steps 4-8, 9-12 */
-        for (int m = (sweep == 0 ? 1 : 2); m <= p; ++m) {
-            double am = a[m - 1];
+        for (int idx = (sweep == 0 ? 0 : 1); idx < p; ++idx) {
+            double am = a[order[idx]];
             mv(ctx, prev, Ay); ++*matvecs;
             for (long i = 0; i < N; ++i)                           /* steps 6 and 10 */
                 ynext[i] = (yn[i] + tau * am * prev[i] + tau * (ghat[i] - Ay[i]))
@@ -229,7 +268,7 @@ static int lim_core(or_matvec_fn mv, void *ctx, long N, const double *ghat,
             memcpy(prev, ynext, N * sizeof(double));               /* steps 7 and 11 */
         }
     }
-    free(beta); free(a); free(prev); free(Ay);
+    free(order); free(beta); free(a); free(prev); free(Ay);
     return p;
 }
 
@@ -624,6 +663,7 @@ int or_integrate(const or_grid *g, const or_params *prm, double *y, or_stats *st
                             &taken, &jexit, st);
         } else {                                                     /* steps 6-7, Fig. 3 */
             p = or_lim_step(g, y, tau, ynext, &lmax, &st->matvecs);
+            if (p < 0) rc = 4;
         }
         if (rc != 0) break;
         for (long i = 0; i < N; ++i)

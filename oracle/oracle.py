@@ -84,6 +84,7 @@ def lib():
                 "or_jacvec": (None, [G, _D, _D, _D]),
                 "or_lambda_max": (C.c_double, [G, _D]),
                 "or_cheb_order": (C.c_int, [C.c_double, C.c_double]),
+                "or_lim_order": (C.c_int, [C.c_int, np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")]),
                 "or_lim_step": (C.c_int, [G, _D, C.c_double, _D, C.POINTER(C.c_double),
                                           C.POINTER(C.c_long)]),
                 "or_lim_dense": (C.c_int, [C.c_long, _D, _D, _D, C.c_double, C.c_double, _D]),
@@ -163,6 +164,13 @@ def lambda_max(g: Grid, y) -> float:
 
 def cheb_order(tau: float, lmax: float) -> int:
     return lib().or_cheb_order(tau, lmax)
+
+
+def lim_order(p: int):
+    """0-based order of the Chebyshev parameters used by the LIM step (Fig. 1 step 2)."""
+    o = np.zeros(p, dtype=np.int32)
+    assert lib().or_lim_order(p, o) == 0
+    return o
 
 
 def lim_step(g: Grid, y, tau: float):

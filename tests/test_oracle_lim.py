@@ -41,7 +41,8 @@ def test_modes_at_nodes_are_implicit_euler(oracle, taulam):
     out, p2 = oracle.lim_dense(np.diag(lam), g, y, tau, lmax)
     assert p2 == p
     ie = (y + tau * g) / (1 + tau * lam)          # implicit Euler, Eq. (EBlin)
-    np.testing.assert_allclose(out, ie, rtol=1e-12, atol=1e-12 * np.abs(ie).max())
+    tol = 1e-14 * max(taulam, 1.0)                # rounding grows like u * tau lambda_max
+    np.testing.assert_allclose(out, ie, rtol=tol, atol=tol * np.abs(ie).max())
 
 
 @pytest.mark.parametrize("taulam", [2.0, 50.0, 1e3, 1e5])
@@ -85,3 +86,58 @@ def test_grid_lim_matches_dense_lim(oracle):
         assert p == p2 and mv == 2 * p - 1
         assert abs(lm - lmax) < 1e-13 * lmax
         np.testing.assert_allclose(out, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def _alphas(p, X):
+    beta = np.cos(np.pi * (2 * np.arange(1, p + 1) - 1) / (2 * p))
+    return X / (1 + beta[0]) * (beta[0] - beta)
+
+
+def _growth_times_tail(p, X, order, npts):
+    """max over iterations k of (1 + X max|head_k|) * max|tail after k|: rounding errors of
+    size ~ u X |iterate| made at iteration k, amplified by the factors still to come."""
+    a = _alphas(p, X)
+    x = np.linspace(0, X, npts)
+    seq = list(order) + list(order[1:])
+    Q = np.array([(a[m] - x) / (1 + a[m]) for m in seq])
+    n = len(seq)
+    H = np.ones(n + 1); h = np.ones_like(x)
+    for k in range(n):
+        h = h * Q[k]; H[k + 1] = np.abs(h).max()
+    T = np.ones(n + 1); t = np.ones_like(x)
+    for k in range(n - 1, -1, -1):
+        T[k] = np.abs(t).max(); t = t * Q[k]
+    return max((1 + X * H[k]) * T[k] for k in range(n))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 8, 21, 40, 64, 125])
+def test_lim_order_keeps_roundoff_growth_near_square_of_tau_lambda(oracle, p):
+    """Fig. 1 step 2: the order starts with beta_1 and is a permutation; its rounding-error
+    growth stays within 3 (tau lambda_max)^2, whereas the natural order exceeds 1e13 at
+    p = 21 and overflows double precision beyond p ~ 150."""
+    order = oracle.lim_order(p)
+    assert order[0] == 0 and sorted(order) == list(range(p))
+    Xp = np.tan(np.pi / 2 - np.pi / (4 * p)) ** 2
+    J = _growth_times_tail(p, Xp, order, 40 * p + 1)
+    assert J <= 3 * max(Xp, 1.0) ** 2
+    if p == 21:
+        assert _growth_times_tail(p, Xp, list(range(p)), 40 * p + 1) > 1e12
+
+
+@pytest.mark.parametrize("taulam", [3e3, 1e5])
+def test_lim_large_p_matches_product_formula(oracle, taulam):
+    """With many Chebyshev factors the step must still equal, up to round-off, the exact
+    error propagation y_IE + prod_m q_m(tau lam) (y^n - y_IE) of the two sweeps."""
+    lmax = 1.0
+    tau = taulam / lmax
+    lam = np.linspace(0.0, lmax, 513)
+    rng = np.random.default_rng(4)
+    g = rng.standard_normal(lam.size); y = rng.standard_normal(lam.size)
+    out, p = oracle.lim_dense(np.diag(lam), g, y, tau, lmax)
+    a = _alphas(p, lmax)
+    R = np.ones_like(lam)
+    for m in list(range(p)) + list(range(1, p)):
+        R = R * (tau * a[m] - tau * lam) / (1 + tau * a[m])
+    ie = (y + tau * g) / (1 + tau * lam)
+    ref = ie + R * (y - ie)
+    assert np.linalg.norm(out - ref) <= 1e-10 * np.linalg.norm(ref)
