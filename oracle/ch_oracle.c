@@ -357,8 +357,8 @@ int or_expm(int n, const double *M, double *E) {
         for (int i = 0; i < n; ++i) s += fabs(M[i * n + j]);
         if (s > norm1) norm1 = s;
     }
-    int sq = 0;
-    if (norm1 > theta13) sq = (int)ceil(log2(norm1 / theta13));
+    int sq = 0;                                  /* least sq >= 0 with norm1/2^sq <= theta13 */
+    for (double sc = norm1; sc > theta13 && sq < 1100; sc *= 0.5) ++sq;
     double scale = ldexp(1.0, -sq);
     for (int i = 0; i < n * n; ++i) X[i] = M[i] * scale;
     mat_mul(n, X, X, X2); mat_mul(n, X2, X2, X4); mat_mul(n, X4, X2, X6);
