@@ -1,0 +1,186 @@
+/*
+ * ch.h -- C ABI of the GB300 (sm_103a) library for the explicit Cahn-Hilliard time
+ * integrators of M.A. Botchev, "Explicit adaptive time stepping for the Cahn-Hilliard
+ * equation by exponential Krylov subspace and Chebyshev polynomial methods",
+ * arXiv:2502.14589.
+ *
+ * Problem (Sec. 2, Eq. IVP): y'(t) = -A (F'(y) + eps^2 A y), F'(y) = y^3 - y, where -A is the
+ * second-order finite-difference Laplacian on a periodic grid of the unit square (dim = 2)
+ * or cube (dim = 3), h_a = 1/n_a, points stored x fastest: index = i0 + n0 (i1 + n1 i2).
+ * Linearisation at y^n (Sec. 3.1, Eqs. J, A_g):
+ *   J_n = 3 diag((y^n)^2) - I,   A_hat_n = A (J_n + eps^2 A),   g_hat^n = A (J_n y^n - F'(y^n));
+ * with the Eyre splitting (Sec. 3.2, Eq. A_g_cs) A_hat_n gains + A and g_hat^n gains + A y^n.
+ *
+ * Conventions for every call below:
+ *  - Vector arguments are CALLER-OWNED DEVICE pointers to N = n0 n1 n2 contiguous doubles
+ *    (FP64 at the boundary in every precision mode), 8-byte aligned.  The library keeps
+ *    no reference to them after the call returns.
+ *  - The grid owns all workspace (Krylov basis, Hessenberg matrix, scratch vectors),
+ *    allocated once by ch_create_grid; no call allocates device memory afterwards.
+ *  - Work is queued on the grid's CUDA stream.  Calls that return host scalars
+ *    (norms, tau_used, est, p_used, lambda_max, stats) synchronise that stream before
+ *    returning; ch_rhs / ch_jacvec with NULL scalar outputs are asynchronous.
+ *  - Errors are returned as ch_status codes; no C++ exception crosses the ABI.  The
+ *    message of the last error on the calling thread is available from ch_last_error().
+ *    Device-side failures (non-finite values, Krylov non-convergence, bounded-wait
+ *    timeouts) are written to a device status word and returned by the next call that
+ *    synchronises.
+ *  - A grid may be used by one host thread at a time.
+ */
+#ifndef CH_H_
+#define CH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CH_OK = 0,
+    CH_EINVAL = 1,        /* invalid argument (sizes, pointers, parameters) */
+    CH_ENOMEM = 2,        /* device or pinned-host allocation failed at create time */
+    CH_ECUDA = 3,         /* a CUDA runtime call failed */
+    CH_ENOTCONV = 4,      /* Krylov run found no admissible step, or step/restart cap hit */
+    CH_ENONFINITE = 5,    /* a NaN or Inf appeared in a reduction or in the solution */
+    CH_ETIMEOUT = 6       /* a bounded device-side wait gave up */
+} ch_status;
+
+typedef enum {
+    CH_FP64 = 0,          /* every vector, stencil and reduction in FP64 */
+    CH_MIXED = 1          /* FP32 stencil arithmetic and Krylov basis; FP64 solution,
+                             inner products, norms, Hessenberg matrix, projected phi,
+                             Chebyshev coefficients and step control */
+} ch_precision;
+
+typedef enum { CH_EE2 = 0, CH_LIM = 1 } ch_scheme;
+
+typedef struct ch_grid ch_grid;       /* opaque */
+
+/* Parameters of a time integration; the "Given" boxes of Fig. 3 (LIM) and Fig. 4 (EE2). */
+typedef struct {
+    int scheme;           /* CH_EE2 or CH_LIM */
+    int adaptive;         /* 1: adaptive tau (Figs. 3, 4); 0: constant tau = tau0 */
+    double T;             /* final time */
+    double tau0;          /* initial (adaptive) or constant step size */
+    double tol;           /* accuracy tolerance of Eqs. (LIMdt), (EEdt), (tol_phi) */
+    int mmax;             /* Krylov dimension m_max (EE2), 1 <= mmax <= capacity */
+    double tol_phi;       /* > 0: fixed Krylov tolerance; <= 0: Eq. (tol_phi) */
+    int eyre;             /* 1: Eyre-splitting A_hat, g_hat of Eq. (A_g_cs) */
+    int64_t max_steps;    /* cap on accepted steps (CH_ENOTCONV when reached before T) */
+} ch_params;
+
+/* Work counters; "matvecs" counts products with A_hat_n as the paper does (Sec. 5.1):
+ * LIM 2p-1 per step, EE2 one per Arnoldi iteration plus one per Krylov start vector. */
+typedef struct {
+    int64_t steps, matvecs, rhs_evals, krylov_iters, restarts, tau_shrinks, phi_evals;
+    double t;             /* time reached */
+    double tau_next;      /* step size the controller proposes next */
+    double last_est;      /* est of the last step (Eq. LIMest) */
+} ch_stats;
+
+/* Create a periodic grid on the unit square (dim 2) or cube (dim 3) with n[a] >= 4 points
+ * per axis (n[2] ignored when dim == 2), parameter eps > 0 of Eq. (IVP), precision mode,
+ * and Krylov basis capacity mmax_capacity (1..128; the basis holds mmax_capacity + 1
+ * vectors).  `cuda_stream` is a cudaStream_t (NULL = legacy default stream) on which all
+ * work of this grid is queued.  Allocates all workspace.  *out receives the handle.     */
+ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
+                         int mmax_capacity, void *cuda_stream, ch_grid **out);
+ch_status ch_destroy_grid(ch_grid *g);
+
+/* Sec. 2, Eq. (IVP): f = -A (F'(y) + eps^2 A y).  Optional host outputs: norm_f = ||f||_2
+ * and norm_ghat = ||g_hat(y)||_2 with g_hat of Eq. (A_g) (or Eq. A_g_cs when `eyre`).     */
+ch_status ch_rhs(ch_grid *g, const double *y, double *f, int eyre, double *norm_f,
+                 double *norm_ghat);
+
+/* Eq. (A_g) / (A_g_cs): w = A_hat(y_lin) v = A (J + eps^2 A [+ I]) v.  Asynchronous.      */
+ch_status ch_jacvec(ch_grid *g, const double *y_lin, const double *v, double *w, int eyre);
+
+/* Fig. 1 step 1: lambda_max = ||A_hat(y)||_1 (host output, synchronises).                */
+ch_status ch_lambda_max(ch_grid *g, const double *y, int eyre, double *lambda_max);
+
+/* Eq. (LIMest): est = ||y1 - y_PC|| / ||y_PC|| with
+ * y_PC = y0 - (tau/2) A (F'(y0) + F'(y1) + eps^2 A (y0 + y1)).  Synchronises.             */
+ch_status ch_estimate(ch_grid *g, const double *y0, const double *y1, double tau, double *est);
+
+/* Fig. 2: one Krylov run for the linearised IVP (Eq. IVPlin) at y_n with tentative step
+ * tau0, tolerance tol_phi (> 0) and dimension mmax.  linear_restart = 0: the run may cut
+ * tau (residual-time step choice, Eq. phi_stop) and *tau_used returns the step taken;
+ * linear_restart = 1: linear residual-time restarting covers all of tau0 (constant-step
+ * use, end of Sec. 4.1).  y_next may not alias y_n.  `stats` (optional) is incremented.  */
+ch_status ch_phi_krylov(ch_grid *g, const double *y_n, double tau0, double tol_phi, int mmax,
+                        int linear_restart, int eyre, double *y_next, double *tau_used,
+                        ch_stats *stats);
+
+/* One EE2 step (Sec. 4, Eqs. IVPlin, EE2) with the Krylov tolerance of prm (Eq. tol_phi
+ * when prm->tol_phi <= 0), linear restarting when prm->adaptive == 0, and the error
+ * estimate of Eq. (LIMest) for the step actually taken.  Synchronises.                    */
+ch_status ch_ee_step(ch_grid *g, const double *y_n, double tau, const ch_params *prm,
+                     double *y_next, double *tau_used, double *est);
+
+/* One LIM step (Sec. 3.1, Fig. 1).  Returns the Chebyshev order p and lambda_max.        */
+ch_status ch_lim_step(ch_grid *g, const double *y_n, double tau, int eyre, double *y_next,
+                      int *p_used, double *lambda_max);
+
+/* Figs. 3 / 4 (adaptive) or constant-step integration of y from t = 0 to T, in place.
+ * Constant steps: ceil(T/tau0) steps, the last one ending exactly at T.  Per-step records
+ * are kept for ch_get_records.                                                            */
+ch_status ch_integrate(ch_grid *g, const ch_params *prm, double *y, ch_stats *stats);
+
+/* Per-step records of the last ch_integrate (host arrays of length >= max; any may be
+ * NULL): step size taken, Krylov dimension at exit of the last run, linear restarts,
+ * 1 if the Krylov residual test cut the step, LIM order p, est.  *count = records kept
+ * (at most the capacity given to ch_set_record_capacity, default 0 = none).              */
+ch_status ch_set_record_capacity(ch_grid *g, int64_t capacity);
+ch_status ch_get_records(ch_grid *g, int64_t max, double *tau, int *jexit, int *restarts,
+                         int *shrunk, int *p, double *est, int64_t *count);
+
+/* Checkpoint state of an integration: time reached and next step size.  ch_set_state
+ * makes the next ch_integrate resume from (t, tau) instead of (0, tau0).                  */
+ch_status ch_get_state(ch_grid *g, double *t, double *tau);
+ch_status ch_set_state(ch_grid *g, double t, double tau);
+
+/* Diagnostics of Sec. 5.2: discrete energy E_h (Eq. Ediscr, read as h^d [sum F(y) +
+ * eps^2/2 sum_a sum ((y_{i+e_a} - y_i)/h_a)^2]) and mass h^d sum y (Eq. m).  Synchronises. */
+ch_status ch_energy_mass(ch_grid *g, const double *y, double *energy, double *mass);
+
+/* Number of kernel launches this grid has issued since creation (for launch accounting). */
+int64_t ch_kernel_launches(const ch_grid *g);
+
+/* Kernel classes of the hot path, for launch accounting and timing (no counterpart in the
+ * paper: these report where the time of Figs. 1-4 goes on the GPU). */
+typedef enum {
+    CH_K_PREP = 0,      /* D, G and min/max of y^2 from y^n (linearisation, Fig. 1 step 1) */
+    CH_K_TSTAGE,        /* stage 1 of A_hat v (Fig. 2 line 4) */
+    CH_K_WSTAGE,        /* stage 2 of A_hat v, fused with h_{1j} */
+    CH_K_MGS,           /* one modified Gram-Schmidt pass (Fig. 2 lines 5-9) */
+    CH_K_PHI,           /* projected phi, residual test, step trace (Fig. 2 lines 10-20) */
+    CH_K_COMBINE,       /* y^n + V_j (beta u) (Fig. 2 line 23) */
+    CH_K_RHS1,          /* stage 1 of f(y) (Eq. IVP) */
+    CH_K_RHS2,          /* stage 2 of f(y), fused with norms and Eq. (LIMest) sums */
+    CH_K_RESID1,        /* stage 1 of g_hat - A_hat x (Fig. 1 steps 6/10, restarts) */
+    CH_K_RESID2,        /* stage 2 of g_hat - A_hat x with its norm (restart vector) */
+    CH_K_LIM2,          /* stage 2 fused with the LIM update (Fig. 1 steps 6/10) */
+    CH_K_ENERGY,        /* energy and mass */
+    CH_K_ARM,           /* Krylov start: beta, tol_phi (Eq. tol_phi) */
+    CH_K_COUNT
+} ch_kernel_class;
+
+/* Start timing every launch of one kernel class with CUDA events recorded on the grid's
+ * stream immediately before and after it (kernel_class = -1 stops timing).  Resets the
+ * accumulated time and the per-class launch counts.                                      */
+ch_status ch_timing_start(ch_grid *g, int kernel_class);
+
+/* Synchronise and report: total event time (ms) and number of timed launches of the timed
+ * class, and per-class launch counts since ch_timing_start (counts may be NULL, else an
+ * array of CH_K_COUNT entries).                                                          */
+ch_status ch_timing_read(ch_grid *g, double *total_ms, int64_t *timed_launches,
+                         int64_t *counts);
+
+/* Message of the last error on the calling thread ("" when none). */
+const char *ch_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CH_H_ */

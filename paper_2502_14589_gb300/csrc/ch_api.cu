@@ -1,0 +1,796 @@
+// ch_api.cu -- C ABI (include/ch.h) and host orchestration of the Cahn-Hilliard hot path.
+//
+// The host queues kernels on the grid's stream and reads back a few scalars once per time
+// step (step size taken, error estimate, lambda_max of the next LIM step).  Inside a Krylov
+// run the host queues Arnoldi iteration j+1 before it waits for the result of iteration j
+// (the device `active` flag, copied to pinned memory), so the GPU never idles on the host;
+// kernels of an iteration queued after convergence return at once.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "ch_internal.cuh"
+
+using ch::Ctrl;
+using ch::Geom;
+using ch::Launch;
+
+static thread_local char g_last_error[512] = "";
+
+static ch_status fail(ch_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(CH_ECUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                                \
+    } while (0)
+
+#define CH_TRY(expr)                        \
+    do {                                    \
+        ch_status s_ = (expr);              \
+        if (s_ != CH_OK) return s_;         \
+    } while (0)
+
+struct StepRecord {
+    double tau, est;
+    int jexit, restarts, shrunk, p;
+};
+
+struct ch_grid {
+    Geom g;
+    int precision;
+    int mmax_cap;
+    cudaStream_t stream;
+    Launch L;
+    int64_t launches;
+    ch::Timing timing;
+    // device workspace
+    double *D, *G, *t, *q;        // per-step coefficients and stage scratch
+    double *F[2];                 // rhs buffers; F[cur] is basis column 0 of a Krylov run
+    double *V;                    // basis columns 1..mmax_cap, stride ldv
+    int64_t ldv;
+    double *y[3];                 // state scratch (ping-pong)
+    float *Vf, *Wf[2], *Df, *tf;  // mixed precision: FP32 basis (slot 0 = Wf[cur]), D, stage
+    double *H;                    // (mmax_cap + 1) x mmax_cap, row-major
+    double *u;                    // mmax_cap
+    double *phi_scratch;
+    double *partials;
+    Ctrl *ctrl;
+    // pinned host mirrors
+    Ctrl *hctrl;
+    int *hflag;
+    cudaEvent_t ev[2];
+    // integration state: (t, tau) reached by the last ch_integrate, and an optional
+    // resume point set by ch_set_state for the next one
+    double t_last, tau_last;
+    double t_resume, tau_resume;
+    int resume;
+    std::vector<StepRecord> rec;
+    int64_t rec_cap;
+};
+
+// ---------------------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------------------
+static ch_status sync_ctrl(ch_grid *g) {
+    CUDA_TRY(cudaMemcpyAsync(g->hctrl, g->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (g->hctrl->status != 0) {
+        const int st = g->hctrl->status;
+        int zero = 0;
+        CUDA_TRY(cudaMemcpyAsync(&g->ctrl->status, &zero, sizeof(int), cudaMemcpyHostToDevice, g->stream));
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+        return fail((ch_status)st, st == CH_ENONFINITE ? "non-finite value in the solution or a reduction"
+                                                       : "Krylov run found no admissible step size");
+    }
+    return CH_OK;
+}
+
+static ch_status check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(CH_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return CH_OK;
+}
+
+static double *basis(ch_grid *g, double *slot0, int c) {   // W_c, 1-based
+    return c == 1 ? slot0 : g->V + (int64_t)(c - 2) * g->ldv;
+}
+
+// Fig. 1 step 1 in closed form: column j of A_hat has the entries
+//   centre  d sigma + eps^2 (sigma^2 + 2 sum_a s_a^2),   +-e_a  -s_a (d + 2 eps^2 sigma),
+//   +-2e_a  eps^2 s_a^2,   +-e_a +-e_b  2 eps^2 s_a s_b   (distinct when every n_a >= 4),
+// so its absolute sum g(d) is convex in d and ||A_hat||_1 = max(g(d_min), g(d_max)).
+static double col_abs_sum(const Geom &G, double d) {
+    const double e2 = G.eps2, sg = G.sigma;
+    double sq = 0.0;
+    for (int a = 0; a < G.dim; ++a) sq += G.s[a] * G.s[a];
+    double r = fabs(d * sg + e2 * (sg * sg + 2.0 * sq));
+    for (int a = 0; a < G.dim; ++a) r += 2.0 * G.s[a] * fabs(d + 2.0 * e2 * sg);
+    for (int a = 0; a < G.dim; ++a) r += 2.0 * e2 * G.s[a] * G.s[a];
+    for (int a = 0; a < G.dim; ++a)
+        for (int b = a + 1; b < G.dim; ++b) r += 8.0 * e2 * G.s[a] * G.s[b];
+    return r;
+}
+
+static double lambda_from_minmax(const Geom &G, double y2min, double y2max, int eyre) {
+    const double shift = eyre ? 1.0 : 0.0;
+    const double dmin = 3.0 * y2min - 1.0 + shift, dmax = 3.0 * y2max - 1.0 + shift;
+    return std::max(col_abs_sum(G, dmin), col_abs_sum(G, dmax));
+}
+
+// Eq. (p)
+static int cheb_order(double tau, double lmax) {
+    const double pi = 3.14159265358979323846;
+    return (int)ceil((pi / 4.0) / (pi / 2.0 - atan(sqrt(tau * lmax))));
+}
+
+// f = rhs(y) into out; mode bits of k_rhs2 (1: ||f||^2, 2: ||g_hat||^2, 4: est sums,
+// 8: half_tau taken from ctrl->tau).
+static void rhs(ch_grid *g, const double *y, double *out, int eyre, int mode,
+                const double *y0 = nullptr, const double *f0 = nullptr, double half_tau = 0.0) {
+    ch::launch_rhs1(g->L, g->g, y, eyre, g->t, (mode & 2) ? g->q : nullptr);
+    ch::launch_rhs2(g->L, g->g, g->t, (mode & 2) ? g->q : nullptr, out, y0, f0, y, half_tau, mode);
+}
+
+struct RunResult {
+    int jexit;
+    double tau;
+    int shrunk;
+    int phi_evals;
+};
+
+// One Krylov run of Fig. 2.  Basis column W_1 is in slot0 and red[0] = ||W_1||^2 (and
+// red[1] = ||g_hat||^2 when use_ghat).  Dm must hold the linearisation coefficients in the
+// basis precision VT.  The result y0 + V_j (beta u) is written to ynext (FP64); the run's
+// scalars are left in ctrl (not synchronised).
+template <typename VT>
+static ch_status krylov_run_t(ch_grid *g, const double *y0, VT *slot0, VT *V, const VT *Dm,
+                              VT *t, double tau0, double tol_phi_fixed, double tol, int use_ghat,
+                              int mmax, double *ynext) {
+    const Launch &L = g->L;
+    const int ldh = g->mmax_cap;
+    auto W = [&](int c) -> VT * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * g->ldv; };
+    ch::launch_krylov_arm(L, tau0, tol_phi_fixed, tol, use_ghat);
+    for (int j = 1; j <= mmax; ++j) {
+        VT *Wj = W(j), *Wn = W(j + 1);
+        ch::launch_tstage<VT>(L, g->g, Wj, Dm, t, 1);
+        ch::launch_wstage<VT>(L, g->g, t, Wn, slot0, &g->H[0 * ldh + (j - 1)], j - 1, 1);
+        for (int k = 1; k <= j; ++k) {
+            const int last = (k == j);
+            ch::launch_mgs<VT>(L, g->g.N, Wn, W(k), last ? nullptr : W(k + 1),
+                               &g->H[(k - 1) * ldh + (j - 1)], last ? nullptr : &g->H[k * ldh + (j - 1)],
+                               k, last);
+        }
+        ch::launch_phi(L, g->H, ldh, j, mmax, g->u, g->phi_scratch);
+        CH_TRY(check_launch());
+        CUDA_TRY(cudaMemcpyAsync(&g->hflag[j & 1], &g->ctrl->active, sizeof(int),
+                                 cudaMemcpyDeviceToHost, g->stream));
+        CUDA_TRY(cudaEventRecord(g->ev[j & 1], g->stream));
+        if (j >= 2) {
+            CUDA_TRY(cudaEventSynchronize(g->ev[(j - 1) & 1]));
+            if (g->hflag[(j - 1) & 1] == 0) break;
+        }
+    }
+    return CH_OK;
+}
+
+// Krylov run on the grid's basis in its precision: slot `s` (0/1) holds W_1 in FP64 (F[s]);
+// mixed grids first round it into the FP32 basis.  Ends with the combine into ynext.
+static ch_status krylov_run(ch_grid *g, const double *y0, int s, double tau0,
+                            double tol_phi_fixed, double tol, int use_ghat, int mmax,
+                            double *ynext) {
+    if (g->precision == CH_FP64) {
+        CH_TRY(krylov_run_t<double>(g, y0, g->F[s], g->V, g->D, g->t, tau0, tol_phi_fixed, tol,
+                                    use_ghat, mmax, ynext));
+        ch::launch_combine(g->L, g->g.N, y0, g->F[s], g->V, g->ldv, ynext);
+    } else {
+        ch::launch_to32(g->L, g->g.N, g->F[s], g->Wf[s]);
+        CH_TRY(krylov_run_t<float>(g, y0, g->Wf[s], g->Vf, g->Df, g->tf, tau0, tol_phi_fixed, tol,
+                                   use_ghat, mmax, ynext));
+        ch::launch_combine32(g->L, g->g.N, y0, g->Wf[s], g->Vf, g->ldv, (float *)g->t, ynext);
+    }
+    return check_launch();
+}
+
+// Linearisation coefficients of A_hat_n at yn (and G for residuals / LIM) in FP64; mixed
+// grids also keep an FP32 copy of D for the Krylov matvecs.
+static void prep(ch_grid *g, const double *yn, int eyre, int want_G, int want_minmax) {
+    ch::launch_prep(g->L, g->g, yn, eyre, g->D, want_G ? g->G : nullptr, want_minmax);
+    if (g->precision == CH_MIXED) ch::launch_to32(g->L, g->g.N, g->D, g->Df);
+}
+
+static void add_record(ch_grid *g, const StepRecord &r) {
+    if ((int64_t)g->rec.size() < g->rec_cap) g->rec.push_back(r);
+}
+
+// ---------------------------------------------------------------------------------------
+// EE2 step (Sec. 4).  On entry F[cur] = f(y_n) with red[0] = ||f||^2 (+ red[1]).
+// adaptive: nonlinear RT step choice; else linear RT restarting over tau.
+// With want_est, f(y_next) goes to F[1-cur] with the est sums of Eq. (LIMest).
+// ---------------------------------------------------------------------------------------
+struct EEOut {
+    double tau, est;
+    int jexit, restarts, shrunk, phi_evals;
+    int64_t matvecs;
+};
+
+static ch_status ee_step_impl(ch_grid *g, const double *yn, int cur, double tau,
+                              double tol_phi_fixed, double tol, int mmax, int linear_restart,
+                              int eyre, double *ynext, int want_est, EEOut *out) {
+    const Launch &L = g->L;
+    const int use_ghat = !(tol_phi_fixed > 0.0);
+    memset(out, 0, sizeof *out);
+    prep(g, yn, eyre, linear_restart, 0);
+    if (!linear_restart) {
+        CH_TRY(krylov_run(g, yn, cur, tau, tol_phi_fixed, tol, use_ghat, mmax, ynext));
+        if (want_est)   // Eq. (LIMest) for the step actually taken (ctrl->tau), f(y_{n+1}) -> F[1-cur]
+            rhs(g, ynext, g->F[1 - cur], eyre, 1 | (use_ghat ? 2 : 0) | 4 | 8, yn, g->F[cur]);
+        CH_TRY(check_launch());
+        CH_TRY(sync_ctrl(g));
+        out->tau = g->hctrl->tau;
+        out->jexit = g->hctrl->jexit;
+        out->shrunk = g->hctrl->shrunk;
+        out->phi_evals = g->hctrl->phi_evals;
+        out->matvecs = 1 + g->hctrl->jexit;
+    } else {
+        // Linear residual-time restarting over the whole step: A_hat_n, g_hat^n stay at y_n;
+        // tol_phi is fixed for the step by the first run (Eq. tol_phi uses beta at y_n).
+        double remaining = tau, tphi = tol_phi_fixed;
+        const double *ycur = yn;
+        int slot = cur;
+        double *dst = ynext;
+        int restarts = 0;
+        for (;;) {
+            CH_TRY(krylov_run(g, ycur, slot, remaining, tphi, tol, use_ghat && restarts == 0, mmax, dst));
+            CH_TRY(sync_ctrl(g));
+            tphi = g->hctrl->tol_phi;
+            out->jexit = g->hctrl->jexit;
+            out->phi_evals += g->hctrl->phi_evals;
+            out->matvecs += 1 + g->hctrl->jexit;
+            const double taken = g->hctrl->tau;
+            if (taken >= remaining) break;
+            remaining -= taken;
+            ycur = dst;
+            dst = (dst == ynext) ? g->y[0] : (dst == g->y[0] ? g->y[1] : g->y[0]);
+            if (++restarts > 100000) return fail(CH_ENOTCONV, "linear restart cap reached");
+            // restart vector W_1 = g_hat^n - A_hat_n y_cur (Fig. 2 line 2)
+            slot = 1 - cur;
+            ch::launch_resid1(L, g->g, ycur, g->D, g->G, g->t);
+            ch::launch_resid2(L, g->g, g->t, g->F[slot]);
+        }
+        if (dst != ynext)
+            CUDA_TRY(cudaMemcpyAsync(ynext, dst, g->g.N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     g->stream));
+        out->restarts = restarts;
+        out->tau = tau;
+        if (want_est) {
+            rhs(g, ynext, g->F[1 - cur], eyre, 1 | (use_ghat ? 2 : 0) | 4, yn, g->F[cur], 0.5 * tau);
+            CH_TRY(check_launch());
+            CH_TRY(sync_ctrl(g));
+        }
+    }
+    if (want_est) out->est = sqrt(g->hctrl->red[2]) / sqrt(g->hctrl->red[3]);
+    return CH_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Order of the Chebyshev parameters (Fig. 1 step 2 fixes only beta_1 first).  The factors
+// of the LIM iterations commute, so the order changes only the growth of rounding errors;
+// this is the recursive mirror-pair order of Lebedev and Finogenov (1971), extended to odd
+// p by placing the middle index right after the first pair.  1-based indices, cached per p.
+// ---------------------------------------------------------------------------------------
+static void mirror_pair_order(int p, std::vector<int> &out) {
+    out.clear();
+    if (p == 1) { out.push_back(1); return; }
+    std::vector<int> half;
+    mirror_pair_order(p / 2, half);
+    for (size_t i = 0; i < half.size(); ++i) {
+        out.push_back(half[i]);
+        out.push_back(p + 1 - half[i]);
+        if (i == 0 && (p % 2 == 1)) out.push_back(p / 2 + 1);
+    }
+}
+
+static const std::vector<int> &cheb_param_order(int p) {
+    static std::mutex mu;
+    static std::map<int, std::vector<int>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(p);
+    if (it != cache.end()) return it->second;
+    std::vector<int> o;
+    mirror_pair_order(p, o);
+    return cache.emplace(p, std::move(o)).first->second;
+}
+
+// ---------------------------------------------------------------------------------------
+// LIM step (Sec. 3.1, Fig. 1) with lambda_max given.
+// ---------------------------------------------------------------------------------------
+static ch_status lim_step_impl(ch_grid *g, const double *yn, double tau, double lmax, int eyre,
+                               double *ynext, int *p_out) {
+    const Launch &L = g->L;
+    const double pi = 3.14159265358979323846;
+    const int p = cheb_order(tau, lmax);                                   // step 1
+    if (p < 1 || p > 1000000) return fail(CH_EINVAL, "Chebyshev order %d out of range", p);
+    std::vector<double> beta(p), a(p);
+    for (int i = 1; i <= p; ++i) beta[i - 1] = cos(pi * (2.0 * i - 1.0) / (2.0 * p));   // 2
+    const double z1 = beta[0];                                             // step 3
+    for (int m = 1; m <= p; ++m) a[m - 1] = lmax / (1.0 + z1) * (z1 - beta[m - 1]);     // 5
+    ch::launch_prep(L, g->g, yn, eyre, g->D, g->G, 0);
+    const std::vector<int> &order = cheb_param_order(p);                   // step 2
+    const double *prev = yn;
+    int it = 0;
+    const int total = 2 * p - 1;
+    for (int sweep = 0; sweep < 2; ++sweep) {                              // steps 4-12
+        for (int idx = (sweep == 0 ? 0 : 1); idx < p; ++idx) {
+            ++it;
+            double *next = (it == total) ? ynext : g->y[it & 1];
+            const double am = a[order[idx] - 1];
+            ch::launch_resid1(L, g->g, prev, g->D, g->G, g->t);
+            ch::launch_lim2(L, g->g, g->t, yn, prev, next, tau * am, tau, 1.0 / (1.0 + tau * am));
+            prev = next;
+        }
+    }
+    *p_out = p;
+    return check_launch();
+}
+
+void ch::Timing::harvest() {
+    if (used == 0) return;
+    cudaEventSynchronize(ev[used - 1]);
+    for (size_t k = 0; k + 1 < used; k += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess) total_ms += ms;
+    }
+    used = 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+ch_status ch_timing_start(ch_grid *g, int kernel_class) {
+    if (!g || kernel_class < -1 || kernel_class >= CH_K_COUNT) return fail(CH_EINVAL, "bad kernel class");
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    g->timing.harvest();
+    if (kernel_class >= 0 && g->timing.ev.empty()) {
+        g->timing.ev.resize(2 * 4096);
+        for (auto &e : g->timing.ev) CUDA_TRY(cudaEventCreate(&e));
+    }
+    g->timing.cls = kernel_class;
+    g->timing.used = 0;
+    g->timing.total_ms = 0.0;
+    g->timing.timed = 0;
+    for (auto &c : g->timing.counts) c = 0;
+    return CH_OK;
+}
+
+ch_status ch_timing_read(ch_grid *g, double *total_ms, int64_t *timed_launches, int64_t *counts) {
+    if (!g) return fail(CH_EINVAL, "null grid");
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    g->timing.harvest();
+    if (total_ms) *total_ms = g->timing.total_ms;
+    if (timed_launches) *timed_launches = g->timing.timed;
+    if (counts) for (int k = 0; k < CH_K_COUNT; ++k) counts[k] = g->timing.counts[k];
+    return CH_OK;
+}
+
+const char *ch_last_error(void) { return g_last_error; }
+
+int64_t ch_kernel_launches(const ch_grid *g) { return g ? g->launches : 0; }
+
+ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
+                         int mmax_capacity, void *cuda_stream, ch_grid **out) {
+    g_last_error[0] = 0;
+    if (!out || !n) return fail(CH_EINVAL, "null argument");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(CH_EINVAL, "dim must be 2 or 3");
+    int64_t N = 1;
+    for (int a = 0; a < dim; ++a) {
+        if (n[a] < 4 || n[a] > (1 << 20)) return fail(CH_EINVAL, "n[%d] = %lld out of range [4, 2^20]", a, (long long)n[a]);
+        N *= n[a];
+    }
+    if (N >= (int64_t)1 << 31) return fail(CH_EINVAL, "grid of %lld points exceeds 2^31 - 1", (long long)N);
+    if (!(eps > 0.0) || !isfinite(eps)) return fail(CH_EINVAL, "eps must be finite and > 0");
+    if (precision != CH_FP64 && precision != CH_MIXED) return fail(CH_EINVAL, "unknown precision");
+    if (mmax_capacity < 1 || mmax_capacity > 128) return fail(CH_EINVAL, "mmax_capacity must be in [1, 128]");
+
+    ch_grid *g = new ch_grid();
+    memset(&g->g, 0, sizeof g->g);
+    g->g.dim = dim;
+    for (int a = 0; a < 3; ++a) g->g.n[a] = a < dim ? (int)n[a] : 1;
+    g->g.N = N;
+    g->g.st[0] = 1; g->g.st[1] = g->g.n[0]; g->g.st[2] = (int64_t)g->g.n[0] * g->g.n[1];
+    g->g.eps2 = eps * eps;
+    g->g.sigma = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        g->g.s[a] = (double)n[a] * (double)n[a];
+        g->g.kap[a] = g->g.eps2 * g->g.s[a];
+        g->g.sigma += 2.0 * g->g.s[a];
+    }
+    g->precision = precision;
+    g->mmax_cap = mmax_capacity;
+    g->stream = (cudaStream_t)cuda_stream;
+    g->launches = 0;
+    g->rec_cap = 0;
+    g->resume = 0;
+    g->t_last = g->tau_last = 0.0;
+
+    auto cleanup_fail = [&](ch_status st, const char *what, cudaError_t e) {
+        ch_destroy_grid(g);
+        return fail(st, "%s: %s", what, cudaGetErrorString(e));
+    };
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cleanup_fail(CH_ECUDA, "device query", e);
+    const int64_t want = (N + ch::kThreads - 1) / ch::kThreads;
+    g->L.blocks = (int)std::min<int64_t>(want, (int64_t)sms * 8);
+    g->L.stream = g->stream;
+    g->L.launches = &g->launches;
+    g->L.timing = &g->timing;
+
+    const int64_t ld = (N + 31) / 32 * 32;     // 256-byte aligned columns
+    g->ldv = ld;
+    const size_t vb = (size_t)ld * sizeof(double);
+    struct { double **p; size_t bytes; } allocs[] = {
+        {&g->D, vb}, {&g->G, vb}, {&g->t, vb}, {&g->q, vb}, {&g->F[0], vb}, {&g->F[1], vb},
+        {&g->y[0], vb}, {&g->y[1], vb}, {&g->y[2], vb},
+        {&g->V, vb * (size_t)mmax_capacity},
+        {&g->H, sizeof(double) * (size_t)(mmax_capacity + 1) * mmax_capacity},
+        {&g->u, sizeof(double) * (size_t)(mmax_capacity + 1)},
+        {&g->phi_scratch, sizeof(double) * (size_t)(6 * (mmax_capacity + 1) * (mmax_capacity + 1) + 2 * (mmax_capacity + 1))},
+        {&g->partials, sizeof(double) * ch::kMaxRed * (size_t)g->L.blocks},
+    };
+    for (auto &a : allocs) {
+        if (precision == CH_MIXED && a.p == &g->V) continue;     // FP32 basis instead
+        e = cudaMalloc((void **)a.p, a.bytes);
+        if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of grid workspace", e); }
+    }
+    if (precision == CH_MIXED) {
+        const size_t fb = (size_t)ld * sizeof(float);
+        struct { float **p; size_t bytes; } fallocs[] = {
+            {&g->Vf, fb * (size_t)mmax_capacity}, {&g->Wf[0], fb}, {&g->Wf[1], fb}, {&g->Df, fb}, {&g->tf, fb}};
+        for (auto &a : fallocs) {
+            e = cudaMalloc((void **)a.p, a.bytes);
+            if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of FP32 basis", e); }
+        }
+    }
+    e = cudaMalloc((void **)&g->ctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of control block", e); }
+    e = cudaMemset(g->ctrl, 0, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaMemset(g->H, 0, sizeof(double) * (size_t)(mmax_capacity + 1) * mmax_capacity);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->hctrl, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->hflag, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = (cudaError_t)ch::phi_setup();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cleanup_fail(CH_ECUDA, "grid set-up", e);
+    g->L.partials = g->partials;
+    g->L.ctrl = g->ctrl;
+    *out = g;
+    return CH_OK;
+}
+
+ch_status ch_destroy_grid(ch_grid *g) {
+    if (!g) return CH_OK;
+    cudaStreamSynchronize(g->stream);
+    double *bufs[] = {g->D, g->G, g->t, g->q, g->F[0], g->F[1], g->y[0], g->y[1], g->y[2],
+                      g->V, g->H, g->u, g->phi_scratch, g->partials};
+    for (double *b : bufs)
+        if (b) cudaFree(b);
+    float *fbufs[] = {g->Vf, g->Wf[0], g->Wf[1], g->Df, g->tf};
+    for (float *b : fbufs)
+        if (b) cudaFree(b);
+    if (g->ctrl) cudaFree(g->ctrl);
+    if (g->hctrl) cudaFreeHost(g->hctrl);
+    if (g->hflag) cudaFreeHost(g->hflag);
+    if (g->ev[0]) cudaEventDestroy(g->ev[0]);
+    if (g->ev[1]) cudaEventDestroy(g->ev[1]);
+    for (auto &e : g->timing.ev) if (e) cudaEventDestroy(e);
+    delete g;
+    return CH_OK;
+}
+
+ch_status ch_rhs(ch_grid *g, const double *y, double *f, int eyre, double *norm_f,
+                 double *norm_ghat) {
+    if (!g || !y || !f) return fail(CH_EINVAL, "null argument");
+    const int mode = (norm_f ? 1 : 0) | (norm_ghat ? 2 : 0);
+    rhs(g, y, f, eyre, mode);
+    CH_TRY(check_launch());
+    if (mode) {
+        CH_TRY(sync_ctrl(g));
+        if (norm_f) *norm_f = sqrt(g->hctrl->red[0]);
+        if (norm_ghat) *norm_ghat = sqrt(g->hctrl->red[1]);
+    }
+    return CH_OK;
+}
+
+ch_status ch_jacvec(ch_grid *g, const double *y_lin, const double *v, double *w, int eyre) {
+    if (!g || !y_lin || !v || !w) return fail(CH_EINVAL, "null argument");
+    ch::launch_prep(g->L, g->g, y_lin, eyre, g->D, nullptr, 0);
+    ch::launch_tstage<double>(g->L, g->g, v, g->D, g->t, 0);
+    ch::launch_wstage<double>(g->L, g->g, g->t, w, nullptr, nullptr, 0, 0);
+    return check_launch();
+}
+
+ch_status ch_lambda_max(ch_grid *g, const double *y, int eyre, double *lambda_max) {
+    if (!g || !y || !lambda_max) return fail(CH_EINVAL, "null argument");
+    ch::launch_prep(g->L, g->g, y, eyre, g->D, nullptr, 1);
+    CH_TRY(check_launch());
+    CH_TRY(sync_ctrl(g));
+    *lambda_max = lambda_from_minmax(g->g, g->hctrl->red[4], g->hctrl->red[5], eyre);
+    return CH_OK;
+}
+
+ch_status ch_estimate(ch_grid *g, const double *y0, const double *y1, double tau, double *est) {
+    if (!g || !y0 || !y1 || !est) return fail(CH_EINVAL, "null argument");
+    rhs(g, y0, g->F[0], 0, 0);
+    rhs(g, y1, g->F[1], 0, 4, y0, g->F[0], 0.5 * tau);
+    CH_TRY(check_launch());
+    CH_TRY(sync_ctrl(g));
+    *est = sqrt(g->hctrl->red[2]) / sqrt(g->hctrl->red[3]);
+    return CH_OK;
+}
+
+ch_status ch_phi_krylov(ch_grid *g, const double *y_n, double tau0, double tol_phi, int mmax,
+                        int linear_restart, int eyre, double *y_next, double *tau_used,
+                        ch_stats *stats) {
+    if (!g || !y_n || !y_next) return fail(CH_EINVAL, "null argument");
+    if (y_n == y_next) return fail(CH_EINVAL, "y_next may not alias y_n");
+    if (mmax < 1 || mmax > g->mmax_cap) return fail(CH_EINVAL, "mmax outside [1, capacity]");
+    if (!(tau0 > 0.0) || !(tol_phi > 0.0)) return fail(CH_EINVAL, "tau0 and tol_phi must be > 0");
+    rhs(g, y_n, g->F[0], eyre, 1);
+    EEOut o;
+    CH_TRY(ee_step_impl(g, y_n, 0, tau0, tol_phi, 0.0, mmax, linear_restart, eyre, y_next, 0, &o));
+    if (tau_used) *tau_used = o.tau;
+    if (stats) {
+        stats->matvecs += o.matvecs;
+        stats->krylov_iters += o.matvecs - 1 - o.restarts;
+        stats->restarts += o.restarts;
+        stats->tau_shrinks += o.shrunk;
+        stats->phi_evals += o.phi_evals;
+        stats->rhs_evals += 1;
+    }
+    return CH_OK;
+}
+
+static ch_status check_params(ch_grid *g, const ch_params *p) {
+    if (!p) return fail(CH_EINVAL, "null params");
+    if (p->scheme != CH_EE2 && p->scheme != CH_LIM) return fail(CH_EINVAL, "unknown scheme");
+    if (!(p->T > 0.0) || !(p->tau0 > 0.0) || !isfinite(p->T) || !isfinite(p->tau0))
+        return fail(CH_EINVAL, "T and tau0 must be finite and > 0");
+    if (p->adaptive && !(p->tol > 0.0)) return fail(CH_EINVAL, "tol must be > 0 for adaptive runs");
+    if (p->scheme == CH_EE2 && (p->mmax < 1 || p->mmax > g->mmax_cap))
+        return fail(CH_EINVAL, "mmax outside [1, capacity]");
+    if (p->scheme == CH_EE2 && !(p->tol_phi > 0.0) && !(p->tol > 0.0))
+        return fail(CH_EINVAL, "need tol_phi > 0 or tol > 0");
+    if (p->max_steps < 1) return fail(CH_EINVAL, "max_steps must be >= 1");
+    return CH_OK;
+}
+
+ch_status ch_ee_step(ch_grid *g, const double *y_n, double tau, const ch_params *prm,
+                     double *y_next, double *tau_used, double *est) {
+    if (!g || !y_n || !y_next) return fail(CH_EINVAL, "null argument");
+    if (y_n == y_next) return fail(CH_EINVAL, "y_next may not alias y_n");
+    CH_TRY(check_params(g, prm));
+    const int use_ghat = !(prm->tol_phi > 0.0);
+    rhs(g, y_n, g->F[0], prm->eyre, 1 | (use_ghat ? 2 : 0));
+    EEOut o;
+    CH_TRY(ee_step_impl(g, y_n, 0, tau, prm->tol_phi, prm->tol, prm->mmax, !prm->adaptive,
+                        prm->eyre, y_next, 1, &o));
+    if (tau_used) *tau_used = o.tau;
+    if (est) *est = o.est;
+    return CH_OK;
+}
+
+ch_status ch_lim_step(ch_grid *g, const double *y_n, double tau, int eyre, double *y_next,
+                      int *p_used, double *lambda_max) {
+    if (!g || !y_n || !y_next) return fail(CH_EINVAL, "null argument");
+    if (y_n == y_next) return fail(CH_EINVAL, "y_next may not alias y_n");
+    if (!(tau > 0.0)) return fail(CH_EINVAL, "tau must be > 0");
+    double lmax;
+    CH_TRY(ch_lambda_max(g, y_n, eyre, &lmax));
+    int p = 0;
+    CH_TRY(lim_step_impl(g, y_n, tau, lmax, eyre, y_next, &p));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (p_used) *p_used = p;
+    if (lambda_max) *lambda_max = lmax;
+    return CH_OK;
+}
+
+ch_status ch_set_record_capacity(ch_grid *g, int64_t capacity) {
+    if (!g || capacity < 0) return fail(CH_EINVAL, "bad argument");
+    g->rec_cap = capacity;
+    g->rec.clear();
+    g->rec.reserve((size_t)std::min<int64_t>(capacity, 1 << 20));
+    return CH_OK;
+}
+
+ch_status ch_get_records(ch_grid *g, int64_t max, double *tau, int *jexit, int *restarts,
+                         int *shrunk, int *p, double *est, int64_t *count) {
+    if (!g) return fail(CH_EINVAL, "null grid");
+    const int64_t n = std::min<int64_t>(max, (int64_t)g->rec.size());
+    for (int64_t k = 0; k < n; ++k) {
+        const StepRecord &r = g->rec[(size_t)k];
+        if (tau) tau[k] = r.tau;
+        if (jexit) jexit[k] = r.jexit;
+        if (restarts) restarts[k] = r.restarts;
+        if (shrunk) shrunk[k] = r.shrunk;
+        if (p) p[k] = r.p;
+        if (est) est[k] = r.est;
+    }
+    if (count) *count = n;
+    return CH_OK;
+}
+
+ch_status ch_get_state(ch_grid *g, double *t, double *tau) {
+    if (!g) return fail(CH_EINVAL, "null grid");
+    if (t) *t = g->t_last;
+    if (tau) *tau = g->tau_last;
+    return CH_OK;
+}
+
+ch_status ch_set_state(ch_grid *g, double t, double tau) {
+    if (!g || !(t >= 0.0) || !(tau > 0.0)) return fail(CH_EINVAL, "bad state");
+    g->t_resume = t;
+    g->tau_resume = tau;
+    g->resume = 1;
+    return CH_OK;
+}
+
+ch_status ch_energy_mass(ch_grid *g, const double *y, double *energy, double *mass) {
+    if (!g || !y) return fail(CH_EINVAL, "null argument");
+    ch::launch_energy(g->L, g->g, y);
+    CH_TRY(check_launch());
+    CH_TRY(sync_ctrl(g));
+    double vol = 1.0;
+    for (int a = 0; a < g->g.dim; ++a) vol /= (double)g->g.n[a];
+    if (energy) *energy = vol * g->hctrl->red[6];
+    if (mass) *mass = vol * g->hctrl->red[7];
+    return CH_OK;
+}
+
+// Step size of constant-step step k: tau0, the last of ceil(T/tau0) steps ending at T.
+static int64_t const_nsteps(double T, double tau0) { return (int64_t)ceil(T / tau0 - 1e-9); }
+static double const_tau(double T, double tau0, int64_t k) {
+    const int64_t n = const_nsteps(T, tau0);
+    if (k < n - 1) return tau0;
+    const double last = T - (double)(n - 1) * tau0;
+    return fabs(last - tau0) <= 1e-9 * tau0 ? tau0 : last;
+}
+
+ch_status ch_integrate(ch_grid *g, const ch_params *prm, double *y, ch_stats *stats) {
+    if (!g || !y) return fail(CH_EINVAL, "null argument");
+    CH_TRY(check_params(g, prm));
+    ch_stats st;
+    memset(&st, 0, sizeof st);
+    g->rec.clear();
+    double t = g->resume ? g->t_resume : 0.0;                              // step 1
+    double tau = g->resume ? g->tau_resume : prm->tau0;
+    g->resume = 0;
+    const int adaptive = prm->adaptive, eyre = prm->eyre;
+    const int64_t nconst = adaptive ? 0 : const_nsteps(prm->T, prm->tau0);
+    const int use_ghat = prm->scheme == CH_EE2 && !(prm->tol_phi > 0.0);
+    // state: ycur (the caller's y, updated in place at the end of each step via swap)
+    double *ycur = y, *ynew = g->y[2];
+    int cur = 0;
+    double lmax = 0.0;
+    // f(y_0) for the first Krylov start vector / the first PC estimate
+    if (prm->scheme == CH_EE2 || adaptive) {
+        rhs(g, ycur, g->F[cur], eyre, 1 | (use_ghat ? 2 : 0));
+        st.rhs_evals += 1;
+    }
+    if (prm->scheme == CH_LIM) {
+        ch::launch_prep(g->L, g->g, ycur, eyre, g->D, nullptr, 1);
+        CH_TRY(check_launch());
+        CH_TRY(sync_ctrl(g));
+        lmax = lambda_from_minmax(g->g, g->hctrl->red[4], g->hctrl->red[5], eyre);
+    }
+    ch_status rc = CH_OK;
+    for (;;) {
+        if (adaptive ? !(t < prm->T) : st.steps >= nconst) break;         // step 2
+        int clipped = 0;
+        if (adaptive) {
+            if (t + tau > prm->T) { tau = prm->T - t; clipped = 1; }      // steps 3-5
+        } else {
+            tau = const_tau(prm->T, prm->tau0, st.steps);
+        }
+        StepRecord r = {tau, 0.0, 0, 0, 0, 0};
+        double taken = tau, est = 0.0;
+        if (prm->scheme == CH_EE2) {                                       // steps 6-8, Fig. 4
+            EEOut o;
+            rc = ee_step_impl(g, ycur, cur, tau, prm->tol_phi, prm->tol, prm->mmax, !adaptive,
+                              eyre, ynew, adaptive, &o);
+            if (rc != CH_OK) break;
+            taken = o.tau; est = o.est;
+            r.jexit = o.jexit; r.restarts = o.restarts; r.shrunk = o.shrunk;
+            st.matvecs += o.matvecs;
+            st.krylov_iters += o.matvecs - 1 - o.restarts;
+            st.restarts += o.restarts;
+            st.tau_shrinks += o.shrunk;
+            st.phi_evals += o.phi_evals;
+            if (adaptive) { st.rhs_evals += 1; cur = 1 - cur; }
+            else {
+                rhs(g, ynew, g->F[cur], eyre, 1 | (use_ghat ? 2 : 0));
+                st.rhs_evals += 1;
+            }
+        } else {                                                           // steps 6-8, Fig. 3
+            int p = 0;
+            rc = lim_step_impl(g, ycur, tau, lmax, eyre, ynew, &p);
+            if (rc != CH_OK) break;
+            r.p = p;
+            st.matvecs += 2 * p - 1;
+            // f(y_{n+1}) with the est sums, and lambda_max of the next step
+            if (adaptive) {
+                ch::launch_rhs1(g->L, g->g, ynew, eyre, g->t, nullptr);
+                ch::launch_rhs2(g->L, g->g, g->t, nullptr, g->F[1 - cur], ycur, g->F[cur], ynew,
+                                0.5 * tau, 4);
+                st.rhs_evals += 1;
+            }
+            ch::launch_prep(g->L, g->g, ynew, eyre, g->D, nullptr, 1);
+            rc = check_launch();
+            if (rc != CH_OK) break;
+            rc = sync_ctrl(g);
+            if (rc != CH_OK) break;
+            if (adaptive) {
+                est = sqrt(g->hctrl->red[2]) / sqrt(g->hctrl->red[3]);
+                cur = 1 - cur;
+            }
+            lmax = lambda_from_minmax(g->g, g->hctrl->red[4], g->hctrl->red[5], eyre);
+        }
+        if (adaptive && !isfinite(est)) { rc = fail(CH_ENONFINITE, "non-finite error estimate"); break; }
+        r.tau = taken; r.est = est;
+        add_record(g, r);
+        std::swap(ycur, ynew);                                             // step 9
+        if (adaptive) t = (clipped && taken == tau) ? prm->T : t + taken;
+        else t = (st.steps + 1 == nconst) ? prm->T : t + taken;
+        ++st.steps;
+        if (adaptive) {                                                    // step 10
+            if (prm->scheme == CH_EE2) {                                   // Eq. (EEdt)
+                const double grow = 1.25 * taken;
+                tau = (est > 0.0) ? std::min(grow, sqrt(prm->tol / est) * taken) : grow;
+            } else {                                                       // Eq. (LIMdt)
+                tau = (est > 0.0) ? (prm->tol / est) * taken : taken;
+            }
+        }
+        if (adaptive && t < prm->T && (!(tau > 0.0) || !isfinite(tau) || t + tau == t)) {
+            rc = fail(CH_ENOTCONV, "step size %g makes no progress at t = %g", tau, t);
+            break;
+        }
+        if (st.steps >= prm->max_steps && (adaptive ? t < prm->T : st.steps < nconst)) {
+            rc = fail(CH_ENOTCONV, "max_steps reached before T");
+            break;
+        }
+    }
+    if (ycur != y) {
+        cudaError_t e = cudaMemcpyAsync(y, ycur, g->g.N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream);
+        if (e != cudaSuccess && rc == CH_OK) rc = fail(CH_ECUDA, "copy of the result: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess && rc == CH_OK) rc = fail(CH_ECUDA, "stream sync: %s", cudaGetErrorString(e));
+    st.t = t;
+    st.tau_next = tau;
+    st.last_est = g->rec.empty() ? 0.0 : g->rec.back().est;
+    g->t_last = t;
+    g->tau_last = tau;
+    if (stats) *stats = st;
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,232 @@
+// ch_internal.cuh -- internal types and device helpers of the GB300 Cahn-Hilliard library.
+//
+// Layout in HBM: every grid vector is N contiguous values, x fastest
+// (index = i0 + n0 (i1 + n1 i2)); the Krylov basis is (mmax_capacity + 1) such vectors,
+// each starting on a 256-byte boundary.  All kernels are grid-stride loops over a fixed
+// number of blocks per grid object, so every reduction is summed in the same order on
+// every run (bit-reproducible): per-thread partial sums, a fixed warp-shuffle/shared-memory
+// tree per block, then the last block to finish (atomic ticket, no waiting) sums the
+// per-block partials in index order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ch.h"
+
+namespace ch {
+
+constexpr int kThreads = 256;          // threads per block of the streaming kernels
+constexpr int kMaxBlocks = 152 * 8;    // 152 SMs x 8 resident blocks of 256 threads
+constexpr int kMaxRed = 4;             // values reduced by one kernel at most
+
+// Periodic grid geometry, passed by value.  -A = discrete Laplacian, h_a = 1/n_a:
+//   (A v)_i = sum_a s_a (2 v_i - v_{i+e_a} - v_{i-e_a}),   s_a = 1/h_a^2 = n_a^2.
+struct Geom {
+    int dim;
+    int n[3];
+    int64_t N;
+    int64_t st[3];      // index stride of each axis: 1, n0, n0 n1
+    double s[3];        // s_a
+    double kap[3];      // eps^2 s_a
+    double sigma;       // 2 sum_a s_a  (diagonal of A)
+    double eps2;        // eps^2
+};
+
+// Device-resident control block of one grid: scalars produced by one kernel and consumed
+// by later kernels or by the host (copied to pinned memory).  Kernels of a Krylov run
+// return immediately once `active` is 0, so the host may queue iterations ahead.
+struct Ctrl {
+    int active;         // 1 while the Arnoldi loop of Fig. 2 runs
+    int jexit;          // Krylov dimension j at exit
+    int status;         // ch_status of the last device-side failure (0 = none)
+    int converged;      // 1: resnorm(tau0) <= tol_phi (Fig. 2 lines 13-14)
+    int shrunk;         // 1: the trace of lines 15-19 cut the step
+    int phi_evals;      // projected-phi evaluations of this run
+    int pad[2];
+    double tau0;        // tentative step of this run
+    double tol_phi;
+    double tau;         // step taken by this run
+    double beta;        // ||v_1|| (Fig. 2 line 2)
+    double rinv;        // 1/beta, then 1/h_{j+1,j}: scale of the next basis vector
+    double hnext2;      // ||w||^2 of the last Arnoldi iteration
+    double resnorm;
+    double red[8];      // generic reduced scalars (norms, est sums, min/max)
+    double gam[130];    // v_c = gam[c-1] W_c: scale of each stored (unnormalised) basis vector
+    double coef[130];   // beta gam_c u_c: coefficients of Fig. 2 line 23
+    double vmean[130];  // mean of each basis vector (mixed-precision mass correction)
+    unsigned int ticket[8];
+};
+
+// ---------------------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void warp_sum(double (&v)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+}
+
+// Block-wide sum of K values; result valid in thread 0.  Fixed tree => deterministic.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K]) {
+    __shared__ double sh[K][kThreads / 32];
+    warp_sum<K>(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[k][wid] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = (lane < (int)(blockDim.x >> 5)) ? sh[k][lane] : 0.0;
+        warp_sum<K>(v);
+    }
+    __syncthreads();
+}
+
+// Each block contributes K partial sums; the last block to arrive sums all partials in
+// block-index order and calls `fin(totals)` on thread 0.  `partials` holds K x gridDim.x
+// doubles, `ticket` is a counter that starts (and is left) at 0.
+template <int K, typename Fin>
+__device__ __forceinline__ void grid_sum(double (&v)[K], double *partials, unsigned int *ticket,
+                                         Fin fin) {
+    __shared__ bool last;
+    block_sum<K>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        acc[k] = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            acc[k] += __ldcg(&partials[k * gridDim.x + b]);
+    }
+    block_sum<K>(acc);
+    if (threadIdx.x == 0) {
+        fin(acc);
+        *ticket = 0u;
+    }
+}
+
+// Min / max variant (for lambda_max): partial pairs reduced with fmin / fmax.
+__device__ __forceinline__ void block_minmax(double &mn, double &mx) {
+    __shared__ double smn[kThreads / 32], smx[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { smn[wid] = mn; smx[wid] = mx; }
+    __syncthreads();
+    if (wid == 0) {
+        mn = (lane < (int)(blockDim.x >> 5)) ? smn[lane] : INFINITY;
+        mx = (lane < (int)(blockDim.x >> 5)) ? smx[lane] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+            mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side launch interface (defined in the .cu files, called by ch_api.cu)
+// ---------------------------------------------------------------------------------------
+// Per-class launch counts, and optional CUDA-event timing of every launch of one class
+// (events recorded on the grid's stream right before and after each such launch).
+struct Timing {
+    int cls = -1;                       // class being timed, -1 = none
+    std::vector<cudaEvent_t> ev;        // 2 events per timed launch
+    size_t used = 0;                    // events in use
+    double total_ms = 0.0;
+    int64_t timed = 0;
+    int64_t counts[CH_K_COUNT] = {0};
+    void harvest();                     // defined in ch_api.cu
+};
+
+struct Launch {
+    int blocks;                 // fixed per grid object
+    cudaStream_t stream;
+    double *partials;           // kMaxRed x blocks
+    Ctrl *ctrl;                 // device control block
+    int64_t *launches;          // host counter of kernel launches
+    Timing *timing;
+};
+
+// RAII bracket around one kernel launch: counts it and, when its class is being timed,
+// records the start/stop events.
+struct LaunchScope {
+    const Launch &L;
+    int cls;
+    bool timed;
+    LaunchScope(const Launch &l, int c) : L(l), cls(c), timed(false) {
+        ++*L.launches;
+        if (!L.timing) return;
+        ++L.timing->counts[c];
+        if (L.timing->cls == c) {
+            if (L.timing->used + 2 > L.timing->ev.size()) L.timing->harvest();
+            if (L.timing->used + 2 <= L.timing->ev.size()) {
+                cudaEventRecord(L.timing->ev[L.timing->used], L.stream);
+                timed = true;
+            }
+        }
+    }
+    ~LaunchScope() {
+        if (!timed) return;
+        cudaEventRecord(L.timing->ev[L.timing->used + 1], L.stream);
+        L.timing->used += 2;
+        ++L.timing->timed;
+    }
+};
+
+// Stencil and streaming kernels, FP64 (ch_stencil.cu)
+void launch_prep(const Launch &L, const Geom &g, const double *y, int eyre, double *D,
+                 double *G, int want_minmax);
+template <typename VT>
+void launch_tstage(const Launch &L, const Geom &g, const VT *x, const VT *D, VT *t, int guarded);
+template <typename VT>
+void launch_wstage(const Launch &L, const Geom &g, const VT *t, VT *w, const VT *v1,
+                   double *hout, int jm1, int guarded);
+template <typename VT>
+void launch_mgs(const Launch &L, int64_t N, VT *w, const VT *vk, const VT *vk1, const double *hk,
+                double *hout, int k, int last);
+void launch_combine32(const Launch &L, int64_t N, const double *y0, const float *v0,
+                      const float *V, int64_t ldv, float *d, double *ynext);
+void launch_to32(const Launch &L, int64_t N, const double *x, float *y);
+void launch_combine(const Launch &L, int64_t N, const double *y0, const double *v0,
+                    const double *V, int64_t ldv, double *ynext);
+void launch_rhs1(const Launch &L, const Geom &g, const double *y, int eyre, double *mu,
+                 double *q);
+void launch_rhs2(const Launch &L, const Geom &g, const double *mu, const double *q,
+                 double *f, const double *y0, const double *f0, const double *y1,
+                 double half_tau, int mode);
+void launch_resid1(const Launch &L, const Geom &g, const double *x, const double *D,
+                   const double *G, double *t);
+void launch_resid2(const Launch &L, const Geom &g, const double *t, double *out);
+void launch_lim2(const Launch &L, const Geom &g, const double *t, const double *yn,
+                 const double *yprev, double *ynext, double tau_a, double tau, double alpha);
+void launch_energy(const Launch &L, const Geom &g, const double *y);
+void launch_krylov_arm(const Launch &L, double tau0, double tol_phi_fixed, double tol,
+                       int use_ghat);
+
+// Projected phi, residual test and step trace of Fig. 2 lines 9-20 (ch_phi.cu)
+int phi_setup();
+void launch_phi(const Launch &L, double *H, int ldh, int j, int mmax, double *u,
+                double *scratch);
+
+}  // namespace ch

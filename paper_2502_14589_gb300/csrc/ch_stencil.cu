@@ -1,0 +1,556 @@
+// ch_stencil.cu -- streaming kernels of the Cahn-Hilliard hot path, FP64.
+//
+// Every operator application is split into two elementwise stages with no redundant halo
+// work (FP64 on GB300 runs at 2 FMA/clk/SM, so the kernels are bound by FP64 instruction
+// issue, not HBM, and the minimum DP-instruction count per point is the design target):
+//   stage 1 (7-point in 3D, 5-point in 2D):  t = D (.) x - sum_a kap_a (x_{+a} + x_{-a})
+//   stage 2:                                 w = c0 t - sum_a c_a (t_{+a} + t_{-a})
+// With D = 3 y^2 - 1 [+1 Eyre] + eps^2 sigma, kap_a = eps^2 s_a, c0 = sigma, c_a = s_a this
+// is A_hat v = A (J + eps^2 A [+ I]) v of Eqs. (A_g), (A_g_cs); other coefficient choices
+// give f(y) of Eq. (IVP), the LIM residual g_hat - A_hat y (Fig. 1 steps 6/10) and the PC
+// estimate of Eq. (LIMest).  Neighbour indices wrap periodically.
+#include <math.h>
+
+#include "ch_internal.cuh"
+
+namespace ch {
+
+__device__ __forceinline__ unsigned nb_p(unsigned i, unsigned c, unsigned n, unsigned st) {
+    return (c + 1u == n) ? i - (n - 1u) * st : i + st;
+}
+__device__ __forceinline__ unsigned nb_m(unsigned i, unsigned c, unsigned n, unsigned st) {
+    return (c == 0u) ? i + (n - 1u) * st : i - st;
+}
+
+// Pair sums x_{+a} + x_{-a} of the neighbours of point i along every axis.
+template <int DIM, typename T>
+__device__ __forceinline__ void pair_sums(const Geom &g, const T *__restrict__ x, unsigned i,
+                                          T (&ps)[3]) {
+    const unsigned n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    const unsigned c0 = i % n0;
+    const unsigned r = i / n0;
+    const unsigned c1 = r % n1;
+    ps[0] = x[nb_p(i, c0, n0, 1u)] + x[nb_m(i, c0, n0, 1u)];
+    ps[1] = x[nb_p(i, c1, n1, n0)] + x[nb_m(i, c1, n1, n0)];
+    if (DIM == 3) {
+        const unsigned n2 = (unsigned)g.n[2], s2 = n0 * n1;
+        const unsigned c2 = r / n1;
+        ps[2] = x[nb_p(i, c2, n2, s2)] + x[nb_m(i, c2, n2, s2)];
+    } else {
+        ps[2] = T(0);
+    }
+}
+
+// Dot-product accumulators.  FP64 vectors: plain FMA accumulation.  FP32 vectors (mixed
+// precision): every product is split exactly into p + e (e = fma(a, b, -p)) and summed with
+// a compensated two-sum in FP32 pairs, so the per-thread sum carries ~2^-44 relative error;
+// the block and grid trees then add in FP64.
+template <typename VT> struct DotAcc;
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+#define GRID_LOOP(i, N) \
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < (unsigned)(N); i += gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------------------------------
+// Per-step preparation from the linearisation point y^n:
+//   D = 3 y^2 - 1 (+1 Eyre) + eps^2 sigma   (diagonal of J_n + eps^2 A [+I] before -kap sums)
+//   G = 2 y^3 (+ y Eyre)                    (= J_n y - F'(y) [+ y], inner part of g_hat)
+//   min / max of y^2                        (Fig. 1 step 1: lambda_max from d_min, d_max)
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_prep(Geom g, const double *__restrict__ y, double dconst, int eyre, double *__restrict__ D,
+       double *__restrict__ G, int want_minmax, double *partials, unsigned int *ticket,
+       Ctrl *ctrl) {
+    double mn = INFINITY, mx = -INFINITY;
+    GRID_LOOP(i, g.N) {
+        const double yi = y[i];
+        const double y2 = yi * yi;
+        D[i] = fma(3.0, y2, dconst);
+        if (G) G[i] = eyre ? fma(2.0 * y2, yi, yi) : 2.0 * y2 * yi;
+        mn = fmin(mn, y2);
+        mx = fmax(mx, y2);
+    }
+    if (!want_minmax) return;
+    block_minmax(mn, mx);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = mn;
+        partials[gridDim.x + blockIdx.x] = mx;
+        __threadfence();
+        last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    mn = INFINITY; mx = -INFINITY;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        mn = fmin(mn, __ldcg(&partials[b]));
+        mx = fmax(mx, __ldcg(&partials[gridDim.x + b]));
+    }
+    block_minmax(mn, mx);
+    if (threadIdx.x == 0) {
+        ctrl->red[4] = mn;
+        ctrl->red[5] = mx;
+        *ticket = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Arnoldi matvec (Fig. 2 line 4) on the unnormalised basis vector x = W_j (v_j = gam_j W_j):
+//   tstage: t = D (.) x - sum_a kap_a (x_{+a} + x_{-a})
+//   wstage: w = gam_j (sigma t - sum_a s_a (t_{+a} + t_{-a}))  = A_hat v_j
+//           and h_{1j} = w . v_1 = gam_1 (w . W_1)           (first pass of lines 5-8)
+// ---------------------------------------------------------------------------------------
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kThreads)
+k_tstage(Geom g, const VT *__restrict__ x, const VT *__restrict__ D, VT *__restrict__ t,
+         const Ctrl *ctrl, int guarded) {
+    if (guarded && !ctrl->active) return;
+    const VT k0 = (VT)g.kap[0], k1 = (VT)g.kap[1], k2 = (VT)g.kap[2];
+    GRID_LOOP(i, g.N) {
+        VT ps[3];
+        pair_sums<DIM>(g, x, i, ps);
+        VT acc = D[i] * x[i];
+        acc = fma(-k0, ps[0], acc);
+        acc = fma(-k1, ps[1], acc);
+        if (DIM == 3) acc = fma(-k2, ps[2], acc);
+        t[i] = acc;
+    }
+}
+
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kThreads)
+k_wstage(Geom g, const VT *__restrict__ t, VT *__restrict__ w, const VT *__restrict__ v1,
+         double *hout, int jm1, double *partials, unsigned int *ticket, Ctrl *ctrl, int guarded) {
+    if (guarded && !ctrl->active) return;
+    const double gam = guarded ? ctrl->gam[jm1] : 1.0;
+    const VT c0 = (VT)(gam * g.sigma), c1 = (VT)(gam * g.s[0]), c2 = (VT)(gam * g.s[1]),
+             c3 = (VT)(gam * g.s[2]);
+    DotAcc<VT> acc;
+    GRID_LOOP(i, g.N) {
+        VT ps[3];
+        pair_sums<DIM>(g, t, i, ps);
+        VT r = c0 * t[i];
+        r = fma(-c1, ps[0], r);
+        r = fma(-c2, ps[1], r);
+        if (DIM == 3) r = fma(-c3, ps[2], r);
+        w[i] = r;
+        if (v1) acc.add(r, v1[i]);
+    }
+    if (!v1) return;
+    double tot1[1] = {acc.value()};
+    grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { *hout = ctrl->gam[0] * tot[0]; });
+}
+
+// ---------------------------------------------------------------------------------------
+// Modified Gram-Schmidt pass k of Fig. 2 lines 5-8, fused with the next dot product:
+//   w -= h_{kj} v_k  (= h_{kj} gam_k W_k),  then  h_{k+1,j} = w . v_{k+1}   (k < j)
+//                                           or    ||w||^2 for line 9       (k = j)
+// ---------------------------------------------------------------------------------------
+template <typename VT>
+__global__ void __launch_bounds__(kThreads)
+k_mgs(int64_t N, VT *__restrict__ w, const VT *__restrict__ vk, const VT *__restrict__ vk1,
+      const double *hk, double *hout, int k, int last, double *partials, unsigned int *ticket,
+      Ctrl *ctrl) {
+    if (!ctrl->active) return;
+    const VT c = (VT)(*hk * ctrl->gam[k - 1]);
+    DotAcc<VT> acc;
+    if (!last) {
+        GRID_LOOP(i, N) {
+            const VT r = fma(-c, vk[i], w[i]);
+            w[i] = r;
+            acc.add(r, vk1[i]);
+        }
+        double tot1[1] = {acc.value()};
+        grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { *hout = ctrl->gam[k] * tot[0]; });
+    } else {
+        GRID_LOOP(i, N) {
+            const VT r = fma(-c, vk[i], w[i]);
+            w[i] = r;
+            acc.add(r, r);
+        }
+        double tot1[1] = {acc.value()};
+        grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { ctrl->hnext2 = tot[0]; });
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Fig. 2 line 23: y_next = y0 + V_j (beta u) = y0 + sum_c coef_c W_c, coef_c = beta gam_c u_c.
+// Column 0 is `v0`, columns 1.. start at V with stride ldv.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_combine(int64_t N, const double *__restrict__ y0, const double *__restrict__ v0,
+          const double *__restrict__ V, int64_t ldv, double *__restrict__ ynext,
+          const Ctrl *ctrl) {
+    const int j = ctrl->jexit;
+    __shared__ double coef[130];
+    for (int c = threadIdx.x; c < j; c += blockDim.x) coef[c] = ctrl->coef[c];
+    __syncthreads();
+    GRID_LOOP(i, N) {
+        double acc = 0.0;
+        if (j > 0) acc = coef[0] * v0[i];
+        for (int c = 1; c < j; ++c) acc = fma(coef[c], V[(c - 1) * ldv + i], acc);
+        ynext[i] = y0[i] + acc;
+    }
+}
+
+// Mixed precision, pass 1: increment d = sum_c coef_c W_c in FP32 and its sum (mass) in
+// compensated FP32 -> FP64 (red[6]).
+__global__ void __launch_bounds__(kThreads)
+k_combine32a(int64_t N, const float *__restrict__ v0, const float *__restrict__ V, int64_t ldv,
+             float *__restrict__ d, double *partials, unsigned int *ticket, Ctrl *ctrl) {
+    const int j = ctrl->jexit;
+    __shared__ float coef[130];
+    for (int c = threadIdx.x; c < j; c += blockDim.x) coef[c] = (float)ctrl->coef[c];
+    __syncthreads();
+    DotAcc<float> acc;
+    GRID_LOOP(i, N) {
+        float a = 0.f;
+        if (j > 0) a = coef[0] * v0[i];
+        for (int c = 1; c < j; ++c) a = fmaf(coef[c], V[(c - 1) * ldv + i], a);
+        d[i] = a;
+        acc.add(a, 1.0f);
+    }
+    double tot1[1] = {acc.value()};
+    grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { ctrl->red[6] = tot[0]; });
+}
+
+// Mixed precision, pass 2: y_next = y0 + (d - mean(d)); the increment of every Krylov step
+// has zero mean in exact arithmetic (columns of A sum to zero, Eq. m), so removing the mean
+// the FP32 rounding left keeps the mass to FP64 rounding.
+__global__ void __launch_bounds__(kThreads)
+k_combine32b(int64_t N, const double *__restrict__ y0, const float *__restrict__ d,
+             double *__restrict__ ynext, const Ctrl *ctrl) {
+    const double mean = ctrl->jexit > 0 ? ctrl->red[6] / (double)N : 0.0;
+    GRID_LOOP(i, N) ynext[i] = y0[i] + ((double)d[i] - mean);
+}
+
+// FP64 -> FP32 copy (start vector of a mixed-precision Krylov run) and FP32 D.
+__global__ void __launch_bounds__(kThreads)
+k_to32(int64_t N, const double *__restrict__ x, float *__restrict__ y) {
+    GRID_LOOP(i, N) y[i] = (float)x[i];
+}
+
+// ---------------------------------------------------------------------------------------
+// Right-hand side of Eq. (IVP), f = -A mu with mu = F'(y) + eps^2 A y, and the pieces the
+// schemes need from the same pass:
+//   rhs1: mu = (y^2 + eps^2 sigma - 1) y - sum_a kap_a (y_{+a} + y_{-a}); q = 2y^3 [+ y]
+//   rhs2: f = -(sigma mu - sum_a s_a (mu_{+a} + mu_{-a}));  g_hat = A q   (Eq. A_g)
+//         mode bit 0: ||f||^2 -> red[0];  bit 1: ||g_hat||^2 -> red[1];
+//         bit 2: Eq. (LIMest) sums with y_PC = y0 + tau/2 (f0 + f(y1)):
+//                ||y1 - y_PC||^2 -> red[2], ||y_PC||^2 -> red[3]
+//         bit 3: tau of the estimate is the step the Krylov run took (ctrl->tau)
+// ---------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_rhs1(Geom g, const double *__restrict__ y, int eyre, double *__restrict__ mu,
+       double *__restrict__ q) {
+    const double cshift = g.eps2 * g.sigma - 1.0;
+    GRID_LOOP(i, g.N) {
+        double ps[3];
+        pair_sums<DIM>(g, y, i, ps);
+        const double yi = y[i];
+        const double y2 = yi * yi;
+        double m = (y2 + cshift) * yi;
+        m = fma(-g.kap[0], ps[0], m);
+        m = fma(-g.kap[1], ps[1], m);
+        if (DIM == 3) m = fma(-g.kap[2], ps[2], m);
+        mu[i] = m;
+        if (q) q[i] = eyre ? fma(2.0 * y2, yi, yi) : 2.0 * y2 * yi;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_rhs2(Geom g, const double *__restrict__ mu, const double *__restrict__ q,
+       double *__restrict__ f, const double *__restrict__ y0, const double *__restrict__ f0,
+       const double *__restrict__ y1, double half_tau, int mode, double *partials,
+       unsigned int *ticket, Ctrl *ctrl) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (mode & 8) half_tau = 0.5 * ctrl->tau;
+    GRID_LOOP(i, g.N) {
+        double ps[3];
+        pair_sums<DIM>(g, mu, i, ps);
+        double r = -g.sigma * mu[i];
+        r = fma(g.s[0], ps[0], r);
+        r = fma(g.s[1], ps[1], r);
+        if (DIM == 3) r = fma(g.s[2], ps[2], r);
+        f[i] = r;
+        if (mode & 1) acc[0] = fma(r, r, acc[0]);
+        if (mode & 2) {
+            double qs[3];
+            pair_sums<DIM>(g, q, i, qs);
+            double gh = g.sigma * q[i];
+            gh = fma(-g.s[0], qs[0], gh);
+            gh = fma(-g.s[1], qs[1], gh);
+            if (DIM == 3) gh = fma(-g.s[2], qs[2], gh);
+            acc[1] = fma(gh, gh, acc[1]);
+        }
+        if (mode & 4) {
+            const double ypc = fma(half_tau, f0[i] + r, y0[i]);
+            const double d = y1[i] - ypc;
+            acc[2] = fma(d, d, acc[2]);
+            acc[3] = fma(ypc, ypc, acc[3]);
+        }
+    }
+    if (!(mode & 7)) return;
+    grid_sum<4>(acc, partials, ticket, [&](double (&tot)[4]) {
+        for (int k = 0; k < 4; ++k) ctrl->red[k] = tot[k];
+    });
+}
+
+// ---------------------------------------------------------------------------------------
+// Residual of the linearised implicit Euler system, r = g_hat - A_hat x  (Fig. 1 steps 6/10,
+// and Fig. 2 line 2 for a restart from x = y_cur):
+//   resid1: t = G - D (.) x + sum_a kap_a (x_{+a} + x_{-a})
+//   resid2: r = sigma t - sum_a s_a (t_{+a} + t_{-a}),  ||r||^2 -> red[0]
+//   lim2:   y_next = (y^n + tau a_m y_prev + tau r) / (1 + tau a_m)
+// ---------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_resid1(Geom g, const double *__restrict__ x, const double *__restrict__ D,
+         const double *__restrict__ G, double *__restrict__ t) {
+    GRID_LOOP(i, g.N) {
+        double ps[3];
+        pair_sums<DIM>(g, x, i, ps);
+        double acc = fma(-D[i], x[i], G[i]);
+        acc = fma(g.kap[0], ps[0], acc);
+        acc = fma(g.kap[1], ps[1], acc);
+        if (DIM == 3) acc = fma(g.kap[2], ps[2], acc);
+        t[i] = acc;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_resid2(Geom g, const double *__restrict__ t, double *__restrict__ out, double *partials,
+         unsigned int *ticket, Ctrl *ctrl) {
+    double acc[1] = {0.0};
+    GRID_LOOP(i, g.N) {
+        double ps[3];
+        pair_sums<DIM>(g, t, i, ps);
+        double r = g.sigma * t[i];
+        r = fma(-g.s[0], ps[0], r);
+        r = fma(-g.s[1], ps[1], r);
+        if (DIM == 3) r = fma(-g.s[2], ps[2], r);
+        out[i] = r;
+        acc[0] = fma(r, r, acc[0]);
+    }
+    grid_sum<1>(acc, partials, ticket, [&](double (&tot)[1]) { ctrl->red[0] = tot[0]; });
+}
+
+// y_next = alpha (y^n + tau a y_prev + tau r) with alpha = 1/(1 + tau a) and r = A t; alpha tau
+// is folded into the stage-2 coefficients: y_next = fma(alpha tau a, y_prev, fma(alpha, y^n, r'')).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_lim2(Geom g, const double *__restrict__ t, const double *__restrict__ yn,
+       const double *__restrict__ yprev, double *__restrict__ ynext, double tau_a, double tau,
+       double alpha) {
+    const double at = alpha * tau;
+    const double c0 = at * g.sigma, c1 = at * g.s[0], c2 = at * g.s[1], c3 = at * g.s[2];
+    const double ca = alpha * tau_a;
+    GRID_LOOP(i, g.N) {
+        double ps[3];
+        pair_sums<DIM>(g, t, i, ps);
+        double r = c0 * t[i];
+        r = fma(-c1, ps[0], r);
+        r = fma(-c2, ps[1], r);
+        if (DIM == 3) r = fma(-c3, ps[2], r);
+        ynext[i] = fma(ca, yprev[i], fma(alpha, yn[i], r));
+    }
+}
+
+// Energy of Eq. (Ediscr) (periodic forward differences) and mass: red[6], red[7] (unscaled
+// sums; the host multiplies by h^d).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_energy(Geom g, const double *__restrict__ y, double *partials, unsigned int *ticket,
+         Ctrl *ctrl) {
+    double acc[2] = {0.0, 0.0};
+    const unsigned n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    GRID_LOOP(i, g.N) {
+        const double yi = y[i];
+        const double u = 1.0 - yi * yi;
+        double e = 0.25 * u * u;
+        const unsigned c0 = i % n0, r = i / n0, c1 = r % n1;
+        double d0 = (y[nb_p(i, c0, n0, 1u)] - yi) * (double)g.n[0];
+        double d1 = (y[nb_p(i, c1, n1, n0)] - yi) * (double)g.n[1];
+        double gs = d0 * d0 + d1 * d1;
+        if (DIM == 3) {
+            const unsigned c2 = r / n1;
+            double d2 = (y[nb_p(i, c2, (unsigned)g.n[2], n0 * n1)] - yi) * (double)g.n[2];
+            gs += d2 * d2;
+        }
+        acc[0] += fma(0.5 * g.eps2, gs, e);
+        acc[1] += yi;
+    }
+    grid_sum<2>(acc, partials, ticket, [&](double (&tot)[2]) {
+        ctrl->red[6] = tot[0];
+        ctrl->red[7] = tot[1];
+    });
+}
+
+// ---------------------------------------------------------------------------------------
+// Krylov start (Fig. 2 line 2) from the norms left in red[] by rhs2 / resid2:
+// beta = ||W_1||, gam_1 = 1/beta; tol_phi by Eq. (tol_phi) unless fixed (> 0).
+// beta == 0 (stationary linear IVP) leaves the run inactive with jexit = 0, y_next = y0.
+// ---------------------------------------------------------------------------------------
+__global__ void k_krylov_arm(Ctrl *ctrl, double tau0, double tol_phi_fixed, double tol,
+                             int use_ghat) {
+    const double beta = sqrt(ctrl->red[0]);
+    ctrl->beta = beta;
+    ctrl->tau0 = tau0;
+    ctrl->tau = tau0;
+    ctrl->jexit = 0;
+    ctrl->converged = 0;
+    ctrl->shrunk = 0;
+    ctrl->phi_evals = 0;
+    ctrl->hnext2 = 0.0;
+    ctrl->resnorm = 0.0;
+    double tp = tol_phi_fixed;
+    if (!(tp > 0.0)) {
+        const double ng = use_ghat ? sqrt(ctrl->red[1]) : 0.0;
+        double a = ng / (10.0 * beta);
+        double m = a < 0.1 ? a : 0.1;
+        if (10.0 * tol < m) m = 10.0 * tol;
+        tp = m > 1e-7 ? m : 1e-7;
+    }
+    ctrl->tol_phi = tp;
+    if (!isfinite(beta)) {
+        ctrl->status = CH_ENONFINITE;
+        ctrl->active = 0;
+        return;
+    }
+    ctrl->active = beta > 0.0 ? 1 : 0;
+    ctrl->gam[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+// ---------------------------------------------------------------------------------------
+// Host launchers.  All reductions use ticket 0: kernels of one grid are serialised on its
+// stream, and the last block of each kernel resets the ticket before the kernel ends.
+// ---------------------------------------------------------------------------------------
+#define DISPATCH_DIM(CLS, g, KERNEL, ...)                                              \
+    do {                                                                               \
+        LaunchScope scope_(L, CLS);                                                    \
+        if ((g).dim == 3) KERNEL<3><<<L.blocks, kThreads, 0, L.stream>>>(__VA_ARGS__); \
+        else KERNEL<2><<<L.blocks, kThreads, 0, L.stream>>>(__VA_ARGS__);              \
+    } while (0)
+
+void launch_prep(const Launch &L, const Geom &g, const double *y, int eyre, double *D,
+                 double *G, int want_minmax) {
+    const double dconst = -1.0 + (eyre ? 1.0 : 0.0) + g.eps2 * g.sigma;
+    LaunchScope scope(L, CH_K_PREP);
+    k_prep<<<L.blocks, kThreads, 0, L.stream>>>(g, y, dconst, eyre, D, G, want_minmax,
+                                                 L.partials, &L.ctrl->ticket[0], L.ctrl);
+}
+
+#define DISPATCH_DIM_T(CLS, g, KERNEL, VT, ...)                                            \
+    do {                                                                                   \
+        LaunchScope scope_(L, CLS);                                                        \
+        if ((g).dim == 3) KERNEL<3, VT><<<L.blocks, kThreads, 0, L.stream>>>(__VA_ARGS__); \
+        else KERNEL<2, VT><<<L.blocks, kThreads, 0, L.stream>>>(__VA_ARGS__);              \
+    } while (0)
+
+template <typename VT>
+void launch_tstage(const Launch &L, const Geom &g, const VT *x, const VT *D, VT *t, int guarded) {
+    DISPATCH_DIM_T(CH_K_TSTAGE, g, k_tstage, VT, g, x, D, t, L.ctrl, guarded);
+}
+
+template <typename VT>
+void launch_wstage(const Launch &L, const Geom &g, const VT *t, VT *w, const VT *v1,
+                   double *hout, int jm1, int guarded) {
+    DISPATCH_DIM_T(CH_K_WSTAGE, g, k_wstage, VT, g, t, w, v1, hout, jm1, L.partials,
+                   &L.ctrl->ticket[0], L.ctrl, guarded);
+}
+
+template <typename VT>
+void launch_mgs(const Launch &L, int64_t N, VT *w, const VT *vk, const VT *vk1, const double *hk,
+                double *hout, int k, int last) {
+    LaunchScope scope(L, CH_K_MGS);
+    k_mgs<VT><<<L.blocks, kThreads, 0, L.stream>>>(N, w, vk, vk1, hk, hout, k, last, L.partials,
+                                                    &L.ctrl->ticket[0], L.ctrl);
+}
+
+template void launch_tstage<double>(const Launch &, const Geom &, const double *, const double *, double *, int);
+template void launch_tstage<float>(const Launch &, const Geom &, const float *, const float *, float *, int);
+template void launch_wstage<double>(const Launch &, const Geom &, const double *, double *, const double *, double *, int, int);
+template void launch_wstage<float>(const Launch &, const Geom &, const float *, float *, const float *, double *, int, int);
+template void launch_mgs<double>(const Launch &, int64_t, double *, const double *, const double *, const double *, double *, int, int);
+template void launch_mgs<float>(const Launch &, int64_t, float *, const float *, const float *, const double *, double *, int, int);
+
+void launch_combine32(const Launch &L, int64_t N, const double *y0, const float *v0,
+                      const float *V, int64_t ldv, float *d, double *ynext) {
+    {
+        LaunchScope scope(L, CH_K_COMBINE);
+        k_combine32a<<<L.blocks, kThreads, 0, L.stream>>>(N, v0, V, ldv, d, L.partials,
+                                                          &L.ctrl->ticket[0], L.ctrl);
+    }
+    LaunchScope scope(L, CH_K_COMBINE);
+    k_combine32b<<<L.blocks, kThreads, 0, L.stream>>>(N, y0, d, ynext, L.ctrl);
+}
+
+void launch_to32(const Launch &L, int64_t N, const double *x, float *y) {
+    LaunchScope scope(L, CH_K_PREP);
+    k_to32<<<L.blocks, kThreads, 0, L.stream>>>(N, x, y);
+}
+
+void launch_combine(const Launch &L, int64_t N, const double *y0, const double *v0,
+                    const double *V, int64_t ldv, double *ynext) {
+    LaunchScope scope(L, CH_K_COMBINE);
+    k_combine<<<L.blocks, kThreads, 0, L.stream>>>(N, y0, v0, V, ldv, ynext, L.ctrl);
+}
+
+void launch_rhs1(const Launch &L, const Geom &g, const double *y, int eyre, double *mu,
+                 double *q) {
+    DISPATCH_DIM(CH_K_RHS1, g, k_rhs1, g, y, eyre, mu, q);
+}
+
+void launch_rhs2(const Launch &L, const Geom &g, const double *mu, const double *q,
+                 double *f, const double *y0, const double *f0, const double *y1,
+                 double half_tau, int mode) {
+    DISPATCH_DIM(CH_K_RHS2, g, k_rhs2, g, mu, q, f, y0, f0, y1, half_tau, mode, L.partials,
+                 &L.ctrl->ticket[0], L.ctrl);
+}
+
+void launch_resid1(const Launch &L, const Geom &g, const double *x, const double *D,
+                   const double *G, double *t) {
+    DISPATCH_DIM(CH_K_RESID1, g, k_resid1, g, x, D, G, t);
+}
+
+void launch_resid2(const Launch &L, const Geom &g, const double *t, double *out) {
+    DISPATCH_DIM(CH_K_RESID2, g, k_resid2, g, t, out, L.partials, &L.ctrl->ticket[0], L.ctrl);
+}
+
+void launch_lim2(const Launch &L, const Geom &g, const double *t, const double *yn,
+                 const double *yprev, double *ynext, double tau_a, double tau, double alpha) {
+    DISPATCH_DIM(CH_K_LIM2, g, k_lim2, g, t, yn, yprev, ynext, tau_a, tau, alpha);
+}
+
+void launch_energy(const Launch &L, const Geom &g, const double *y) {
+    DISPATCH_DIM(CH_K_ENERGY, g, k_energy, g, y, L.partials, &L.ctrl->ticket[0], L.ctrl);
+}
+
+void launch_krylov_arm(const Launch &L, double tau0, double tol_phi_fixed, double tol,
+                       int use_ghat) {
+    LaunchScope scope(L, CH_K_ARM);
+    k_krylov_arm<<<1, 1, 0, L.stream>>>(L.ctrl, tau0, tol_phi_fixed, tol, use_ghat);
+}
+
+}  // namespace ch

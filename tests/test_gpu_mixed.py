@@ -1,0 +1,83 @@
+"""Mixed precision (FP32 Krylov basis and stencil arithmetic, FP64 solution, reductions,
+Hessenberg matrix, projected phi and control) against the FP64 oracle.  The tolerance of a
+single Krylov step comes from the arithmetic: FP32 basis vectors perturb A_hat by about
+u32 ||A_hat||, which moves the increment by about u32 * tau * lambda_max relative to it."""
+import numpy as np
+import pytest
+
+from paper_2502_14589_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def ch():
+    from paper_2502_14589_gb300 import build, ch as chmod
+    build.build()
+    chmod.load()
+    return chmod
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("dim,n,eps,tau", [(2, (128, 128), 0.02, 2e-7), (2, (256, 256), 0.01, 2e-8),
+                                           (3, (32, 32, 32), 0.03, 1e-6)])
+def test_mixed_krylov_step(ch, oracle, dim, n, eps, tau):
+    y = inputs.initial_state(n, 3, -0.05, 0.05)
+    og = oracle.Grid(dim, n, eps)
+    lmax = oracle.lambda_max(og, y)
+    with ch.Grid(dim, n, eps, ch.CH_MIXED) as G:
+        yn = torch.empty(G.N, dtype=torch.float64, device="cuda")
+        tu, st = ch.ch_phi_krylov(G.h, dev(y), tau, 1e-7, 30, 0, yn)
+        yg = host(yn)
+        _, m1 = ch.ch_energy_mass(G.h, yn)
+        _, m0 = ch.ch_energy_mass(G.h, dev(y))
+    rc, yo, to, jo, sto = oracle.ee_step(og, y, tu, tol_phi_fixed=1e-7, mmax=30)
+    inc = np.linalg.norm(yo - y)
+    err = np.linalg.norm(yg - yo) / inc
+    bound = 50 * U32 * max(tau * lmax, 1.0)
+    print(f"mixed Krylov step n={n} tau*lmax={tau * lmax:.3g} increment rel err={err:.2e} bound={bound:.2e}")
+    assert err < bound
+    assert abs(m1 - m0) < 1e-13
+
+
+@pytest.mark.parametrize("dim,n,eps,T", [(2, (96, 96), 0.02, 1e-4), (3, (24, 24, 24), 0.04, 1e-4)])
+def test_mixed_adaptive_error_at_T(ch, oracle, dim, n, eps, T):
+    """Adaptive EE2 in mixed precision: relative L2 error at T against the FP64 oracle run
+    of the same scheme and tolerance, stated and held to the 1e-5 target."""
+    y0 = inputs.initial_state(n, 1, -0.05, 0.05)
+    with ch.Grid(dim, n, eps, ch.CH_MIXED) as G:
+        y = dev(y0)
+        st = ch.ch_integrate(G.h, ch.make_params("ee2", True, T, 1e-7, 1e-6, 30), y)
+        yg = host(y)
+    rc, yo, t, sto, rec = oracle.integrate(oracle.Grid(dim, n, eps), y0, "ee2", True, T, 1e-7,
+                                           tol=1e-6, mmax=30)
+    err = np.linalg.norm(yg - yo) / np.linalg.norm(yo)
+    print(f"mixed adaptive EE2 n={n}: steps {st['steps']} vs {sto['steps']}, error at T {err:.2e}")
+    assert st["t"] == T
+    assert err < 1e-5
+    assert abs(yg.mean() - y0.mean()) < 1e-13
+
+
+def test_mixed_grid_lim_runs_fp64(ch, oracle):
+    """LIM iterations amplify rounding by ~ (tau lambda_max)^2, so a mixed grid keeps them in
+    FP64: the result matches the FP64 oracle to FP64 parity."""
+    n = (64, 64)
+    y = inputs.initial_state(n, 2, -0.05, 0.05)
+    with ch.Grid(2, n, 0.05, ch.CH_MIXED) as G:
+        yn = torch.empty(64 * 64, dtype=torch.float64, device="cuda")
+        p, lm = ch.ch_lim_step(G.h, dev(y), 3e-6, yn)
+        yg = host(yn)
+    yo, po, lo, _ = oracle.lim_step(oracle.Grid(2, n, 0.05), y, 3e-6)
+    assert p == po
+    assert np.linalg.norm(yg - yo) / np.linalg.norm(yo) < 1e-12
