@@ -7,7 +7,7 @@ operator applications per second = N x (A_hat products + right-hand-side evaluat
 time, with the time to T of each scheme reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload c1_2d1024_adaptive] [--roofline-kernel mgs]
+                    [--workload c1_2d1024_adaptive]
 
 N > 1 runs under torchrun: every rank integrates its own independently seeded instance
 (replicas of the single-GPU workload, weak scaling) and rank 0 prints the JSON line.
@@ -30,8 +30,13 @@ METRIC = "CH grid-pt updates/s & time-to-T (EE, LIM): mixed/batched vs FP64, ≤
 UNIT = "grid-pt operator applications/s"
 L2_BYTES = 129 * 2 ** 20
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 FMA peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (max SM clock)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2.07 GHz
+FP64_ISSUE_PEAK = 152 * 2 * 2.07e9              # FP64-pipe instructions/s
+FP64_PEAK_TFLOPS = 2 * FP64_ISSUE_PEAK / 1e12   # FMA = 2 flop
+try:
+    HBM_GBS = json.load(open(PEAKS_FILE))["hbm_gbs"]
+except Exception:
+    HBM_GBS = 6800.0                            # fallback when the measured file is absent
 
 
 def parse():
@@ -41,9 +46,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c1_2d1024_adaptive")
-    ap.add_argument("--roofline-kernel", default="mgs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-roofline", action="store_true",
+                    help="skip the per-kernel timing after the timed region (launch-list runs)")
+    ap.add_argument("--t-final", type=float, default=None,
+                    help="integrate to this time instead of the workload's T (profiling runs only)")
     return ap.parse_args()
 
 
@@ -155,6 +164,70 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------------------
+# batched workload: many independent instances of uneven size in one launch sequence
+# ---------------------------------------------------------------------------------------
+def run_batch_workload(args, rank, world, dist):
+    import numpy as np
+    import torch
+    from paper_2502_14589_gb300 import build, ch, inputs
+    build.build()
+    wl = dict(inputs.WORKLOADS[args.workload])
+    if args.t_final is not None:
+        wl["T"] = args.t_final
+    count = wl["count"]
+    sides, eps = inputs.batch_descriptors(count, seed=0)
+    y0s = [inputs.initial_state((int(n), int(n)), 1 + i + 1000 * rank, wl["lo"], wl["hi"])
+           for i, n in enumerate(sides)]
+    Ns = np.array([int(n) * int(n) for n in sides])
+    stream = torch.cuda.current_stream()
+    out = {}
+    for prec, name in ((ch.CH_MIXED, "mixed"), (ch.CH_FP64, "fp64")):
+        h = ch.ch_create_batch(2, [int(n) for n in sides], list(eps), prec, wl["mmax"], stream)
+        offs, chunk = ch.ch_batch_layout(h, count)
+        y0 = torch.zeros(offs[-1], dtype=torch.float64, device="cuda")
+        for i in range(count):
+            y0[offs[i]:offs[i] + Ns[i]] = torch.from_numpy(y0s[i]).cuda()
+        y = torch.empty_like(y0)
+        prm = ch.make_params("ee2", True, wl["T"], wl["tau0"], wl["tol"], wl["mmax"])
+        reps = args.steps if name == "mixed" else 1
+        for _ in range(args.warmup if name == "mixed" else 1):
+            y.copy_(y0); ch.ch_integrate_batch(h, prm, y, count)
+        torch.cuda.synchronize()
+        ms, ops = 0.0, 0
+        for _ in range(reps):
+            y.copy_(y0)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = ch.ch_integrate_batch(h, prm, y, count)
+            e1.record(stream); e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            ops += int(sum(Ns[i] * (st[i]["matvecs"] + st[i]["rhs_evals"]) for i in range(count)))
+        yh = y.cpu().numpy()
+        out[name] = {"ms": ms / reps, "value": ops / (ms * 1e-3), "chunk_len": chunk,
+                     "steps_max": max(x["steps"] for x in st), "steps_sum": sum(x["steps"] for x in st),
+                     "y": [yh[offs[i]:offs[i] + Ns[i]] for i in range(count)],
+                     "launches": ch.ch_batch_kernel_launches(h)}
+        ch.ch_destroy_batch(h)
+    errs = [np.linalg.norm(a - b) / np.linalg.norm(b) for a, b in zip(out["mixed"]["y"], out["fp64"]["y"])]
+    for k in out:
+        out[k].pop("y")
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": out["mixed"]["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["mixed"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {count} 2D periodic instances, sides from {list(inputs.BATCH_SIDES)}, "
+                                   f"eps U[0.01,0.05], u0 U[{wl['lo']},{wl['hi']}] zero-mean, adaptive EE2(m_max="
+                                   f"{wl['mmax']}) tol {wl['tol']} to T={wl['T']}, FP32 Krylov basis/stencils, FP64 "
+                                   f"reductions/phi/control", "global_batch": count, "grid_points": int(Ns.sum())},
+            "batch": out, "mixed_vs_fp64": {"speedup": out["fp64"]["ms"] / out["mixed"]["ms"],
+                                             "max_rel_err_at_T": float(max(errs)),
+                                             "median_rel_err_at_T": float(np.median(errs))},
+        }), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------
 def main():
@@ -173,6 +246,11 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
+    if args.workload.startswith("c3"):
+        run_batch_workload(args, rank, world, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     import numpy as np
     import torch
@@ -180,7 +258,9 @@ def main():
     build.build()
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    wl = inputs.WORKLOADS[args.workload]
+    wl = dict(inputs.WORKLOADS[args.workload])
+    if args.t_final is not None:
+        wl["T"] = args.t_final
     n = [wl["n"]] * wl["dim"]
     N = int(np.prod(n))
     y0_host = inputs.initial_state(n, rank, wl["lo"], wl["hi"], wl["mean"])
@@ -191,11 +271,16 @@ def main():
     G = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_FP64, wl["mmax"], stream)
     prm = {s: ch.make_params(s, True, wl["T"], wl["tau0"], wl["tol"], wl["mmax"]) for s in ("ee2", "lim")}
 
-    def one_step(yin_dev):
+    def one_step(yin_dev, record=None):
         stats = {}
         for s in ("ee2", "lim"):
             y.copy_(yin_dev)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
             stats[s] = ch.ch_integrate(G.h, prm[s], y)
+            e1.record(stream)
+            if record is not None:
+                record[s].append((e0, e1, stats[s]))
         return stats
 
     for _ in range(args.warmup):
@@ -203,7 +288,7 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region: K steps, events per step, L2 flushed between steps --------------
-    ch.ch_timing_start(G.h, args.roofline_kernel)
+    ch.ch_timing_start(G.h, None)           # per-class launch counts, no per-kernel events
     launches0 = ch.ch_kernel_launches(G.h)
     clocks = ClockSampler()
     if rank == 0:
@@ -211,25 +296,23 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, ops, per_scheme = [], 0, {"ee2": [], "lim": []}
+    step_ms, ops, rec = [], 0, {"ee2": [], "lim": []}
     for k in range(args.steps):
         flush.zero_()
         ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        st = one_step(y0)
+        st = one_step(y0, rec)
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
         for s in ("ee2", "lim"):
             ops += N * (st[s]["matvecs"] + st[s]["rhs_evals"])
-            per_scheme[s].append(st[s])
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
     launches = ch.ch_kernel_launches(G.h) - launches0
-    kern_ms, kern_n, counts = ch.ch_timing_read(G.h)
-    ch.ch_timing_start(G.h, None)
+    _, _, counts = ch.ch_timing_read(G.h)
     total_ms = sum(step_ms)
     if dist is not None:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -239,20 +322,38 @@ def main():
         dist.all_reduce(o, op=dist.ReduceOp.SUM)
         ops = float(o.item())
     value = ops / (total_ms * 1e-3)
-
-    # ---- time to T of each scheme (one more run each, events on the stream) -------------
     ttt = {}
     for s in ("ee2", "lim"):
+        ms = [e0.elapsed_time(e1) for e0, e1, _ in rec[s]]
+        st = rec[s][-1][2]
+        ttt[s] = {"ms": sum(ms) / len(ms), "steps": st["steps"], "matvecs": st["matvecs"],
+                  "rhs_evals": st["rhs_evals"], "phi_evals": st["phi_evals"],
+                  "tau_shrinks": st["tau_shrinks"],
+                  "ops_per_s": N * (st["matvecs"] + st["rhs_evals"]) / (sum(ms) / len(ms) * 1e-3)}
+
+    # ---- mixed precision on the same instance: time to T and error at T against FP64 ----
+    mixed = None
+    if not args.no_mixed:
         y.copy_(y0)
+        ch.ch_integrate(G.h, prm["ee2"], y)
+        y_fp64 = y.clone()
+        Gm = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_MIXED, wl["mmax"], stream)
+        ym = torch.empty_like(y0)
+        ym.copy_(y0)
+        ch.ch_integrate(Gm.h, prm["ee2"], ym)            # warm-up (graph capture)
+        ym.copy_(y0)
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        stt = ch.ch_integrate(G.h, prm[s], y)
-        e1.record(stream)
-        e1.synchronize()
-        ttt[s] = {"ms": e0.elapsed_time(e1), "steps": stt["steps"], "matvecs": stt["matvecs"],
-                  "rhs_evals": stt["rhs_evals"], "phi_evals": stt["phi_evals"],
-                  "tau_shrinks": stt["tau_shrinks"]}
+        stm = ch.ch_integrate(Gm.h, prm["ee2"], ym)
+        e1.record(stream); e1.synchronize()
+        ms_m = e0.elapsed_time(e1)
+        err = float(torch.linalg.norm(ym - y_fp64) / torch.linalg.norm(y_fp64))
+        mixed = {"ee2_ms_to_T": ms_m, "ee2_speedup_vs_fp64": ttt["ee2"]["ms"] / ms_m,
+                 "ee2_rel_err_at_T_vs_fp64": err, "steps": stm["steps"], "matvecs": stm["matvecs"],
+                 "ops_per_s": N * (stm["matvecs"] + stm["rhs_evals"]) / (ms_m * 1e-3),
+                 "mass_drift": float(abs(ym.mean() - y0.mean()))}
+        Gm.close()
 
     # ---- end to end through the C ABI with host buffers ----------------------------------
     e2e = None
@@ -260,7 +361,7 @@ def main():
         y_host = torch.from_numpy(y0_host.copy()).pin_memory()
         out_host = torch.empty(N, dtype=torch.float64).pin_memory()
         e2e_ops, e2e_ms = 0, 0.0
-        for k in range(args.steps):
+        for k in range(max(1, args.steps // 2)):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -275,24 +376,85 @@ def main():
         e2e = {"value": e2e_ops / (e2e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": 2 * N * 8}
 
-    # ---- roofline of the timed kernel class -----------------------------------------------
+    # ---- roofline: every streaming kernel class timed on the workload grid ---------------
+    # (CUDA events on the grid's stream around a graph of back-to-back launches); the
+    # dominant class is the one with the largest launches x mean duration in the timed region
+    kernels = {}
+    for cls in (() if args.no_roofline else ("tstage", "wstage", "mgs", "resid1", "lim2", "rhs1", "rhs2")):
+        kb = ch.ch_bench_kernel(G.h, cls, 200)
+        dur = kb["avg_us"] * 1e-6
+        kernels[cls] = {"launches": counts[cls], "avg_us": kb["avg_us"],
+                        "est_share_s": counts[cls] * dur,
+                        "gbs": kb["bytes"] / dur / 1e9, "tflops": kb["flops"] / dur / 1e12,
+                        "fp64_issue_frac": kb["fp64_instr"] / dur / FP64_ISSUE_PEAK,
+                        "bytes": kb["bytes"], "flops": kb["flops"], "fp64_instr": kb["fp64_instr"]}
+    # ---- mixed precision on the same instance: time to T and error at T against FP64 ----
+    mixed = None
+    if not args.no_mixed:
+        y.copy_(y0)
+        ch.ch_integrate(G.h, prm["ee2"], y)
+        y_fp64 = y.clone()
+        Gm = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_MIXED, wl["mmax"], stream)
+        ym = torch.empty_like(y0)
+        ym.copy_(y0)
+        ch.ch_integrate(Gm.h, prm["ee2"], ym)            # warm-up (graph capture)
+        ym.copy_(y0)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stm = ch.ch_integrate(Gm.h, prm["ee2"], ym)
+        e1.record(stream); e1.synchronize()
+        ms_m = e0.elapsed_time(e1)
+        err = float(torch.linalg.norm(ym - y_fp64) / torch.linalg.norm(y_fp64))
+        mixed = {"ee2_ms_to_T": ms_m, "ee2_speedup_vs_fp64": ttt["ee2"]["ms"] / ms_m,
+                 "ee2_rel_err_at_T_vs_fp64": err, "steps": stm["steps"], "matvecs": stm["matvecs"],
+                 "ops_per_s": N * (stm["matvecs"] + stm["rhs_evals"]) / (ms_m * 1e-3),
+                 "mass_drift": float(abs(ym.mean() - y0.mean()))}
+        Gm.close()
+
+    # ---- end to end through the C ABI with host buffers ----------------------------------
+    e2e = None
+    if not args.no_e2e:
+        y_host = torch.from_numpy(y0_host.copy()).pin_memory()
+        out_host = torch.empty(N, dtype=torch.float64).pin_memory()
+        e2e_ops, e2e_ms = 0, 0.0
+        for k in range(max(1, args.steps // 2)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for s in ("ee2", "lim"):
+                y.copy_(y_host, non_blocking=True)
+                st = ch.ch_integrate(G.h, prm[s], y)
+                out_host.copy_(y, non_blocking=True)
+                e2e_ops += N * (st["matvecs"] + st["rhs_evals"])
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+        e2e = {"value": e2e_ops / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": 2 * N * 8}
+
+    # ---- roofline: every streaming kernel class timed on the workload grid ---------------
+    # (CUDA events on the grid's stream around a graph of back-to-back launches); the
+    # dominant class is the one with the largest launches x mean duration in the timed region
+    kernels = {}
+    for cls in (() if args.no_roofline else ("tstage", "wstage", "mgs", "resid1", "lim2", "rhs1", "rhs2")):
+        kb = ch.ch_bench_kernel(G.h, cls, 200)
+        dur = kb["avg_us"] * 1e-6
+        kernels[cls] = {"launches": counts[cls], "avg_us": kb["avg_us"],
+                        "est_share_s": counts[cls] * dur,
+                        "gbs": kb["bytes"] / dur / 1e9, "tflops": kb["flops"] / dur / 1e12,
+                        "fp64_issue_frac": kb["fp64_instr"] / dur / FP64_ISSUE_PEAK,
+                        "bytes": kb["bytes"], "flops": kb["flops"], "fp64_instr": kb["fp64_instr"]}
     roof = None
-    if kern_n > 0:
-        avg_s = kern_ms * 1e-3 / kern_n
-        if args.roofline_kernel == "mgs":
-            # one MGS pass: w -= h v_k and one dot product: 2 FP64 FMA = 4 flop per point
-            flop = 4.0 * N
-            achieved = flop / avg_s / 1e12
-            roof = {"kernel": "k_mgs", "bound": "alu", "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": None, "peak_source": "FP64 FMA rate 152 SM x 2 FMA/clk x 2.07 GHz",
-                    "launches_timed": kern_n, "avg_launch_us": avg_s * 1e6,
-                    "algorithmic_bytes_per_launch": 32.0 * N}
-    hbm = None
-    try:
-        hbm = json.load(open(PEAKS_FILE)).get("hbm_gbs")
-    except Exception:
-        pass
+    if kernels:
+        dom = max(kernels, key=lambda c: kernels[c]["est_share_s"])
+        kd = kernels[dom]
+        roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": kd["tflops"],
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kd["tflops"] / FP64_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "fp64_issue_frac": kd["fp64_issue_frac"], "avg_launch_us": kd["avg_us"],
+                "algorithmic_bytes_per_launch": kd["bytes"], "achieved_gbs": kd["gbs"],
+                "hbm_frac_of_measured": kd["gbs"] / HBM_GBS}
 
     # ---- CPU baseline (oracle on a bounded sample, rank 0 only, N = 1) -----------------
     cpu = None
@@ -313,7 +475,8 @@ def main():
                        "grid_points": N, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed (256 MiB write) before every timed step"},
             "time_to_T": ttt, "e2e": e2e, "gpu_launches": launches, "launches_by_kernel": counts,
-            "roofline": roof, "hbm_peak_gbs_measured": hbm, "cpu_baseline": cpu, "clocks": clk,
+            "mixed": mixed, "roofline": roof, "kernels": kernels, "hbm_peak_gbs": HBM_GBS, "cpu_baseline": cpu,
+            "clocks": clk,
         }
         print(json.dumps(out), flush=True)
     G.close()

@@ -147,6 +147,25 @@ ch_status ch_energy_mass(ch_grid *g, const double *y, double *energy, double *ma
 /* Number of kernel launches this grid has issued since creation (for launch accounting). */
 int64_t ch_kernel_launches(const ch_grid *g);
 
+/* ---- Batches of independent instances ---------------------------------------------------
+ * `count` periodic grids of the same dim with their own sizes (n[3i + a], a < dim, each
+ * >= 4) and eps[i], advanced together with adaptive EE2 (Fig. 4) by ch_integrate_batch: every
+ * instance keeps its own time, step size, Krylov run and controller; one kernel launch serves
+ * all instances still before T.  The states are concatenated in one caller-owned device array
+ * of FP64 values: instance i occupies [offsets[i], offsets[i] + N_i) (offsets from
+ * ch_batch_layout; gaps between instances are ignored).  precision CH_MIXED keeps the Krylov
+ * basis and stencil arithmetic in FP32 as for a single grid.  mmax_capacity <= 63.         */
+typedef struct ch_batch ch_batch;
+ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *eps, int precision,
+                          int mmax_capacity, void *cuda_stream, ch_batch **out);
+ch_status ch_destroy_batch(ch_batch *b);
+/* offsets: count + 1 entries (last = total length of the concatenated array); chunk_len:
+ * values per thread block picked by the creation-time tuner.  Either may be NULL.          */
+ch_status ch_batch_layout(const ch_batch *b, int64_t *offsets, int *chunk_len);
+/* prm: scheme CH_EE2, adaptive 1, no Eyre.  stats (optional) receives `count` entries.    */
+ch_status ch_integrate_batch(ch_batch *b, const ch_params *prm, double *y, ch_stats *stats);
+int64_t ch_batch_kernel_launches(const ch_batch *b);
+
 /* Kernel classes of the hot path, for launch accounting and timing (no counterpart in the
  * paper: these report where the time of Figs. 1-4 goes on the GPU). */
 typedef enum {
@@ -176,6 +195,17 @@ ch_status ch_timing_start(ch_grid *g, int kernel_class);
  * array of CH_K_COUNT entries).                                                          */
 ch_status ch_timing_read(ch_grid *g, double *total_ms, int64_t *timed_launches,
                          int64_t *counts);
+
+/* Time one kernel class in isolation on this grid's current workspace: R back-to-back
+ * launches captured in a CUDA graph, CUDA events on the grid's stream around the graph.
+ * Returns the mean duration of one launch and its algorithmic traffic and arithmetic per
+ * launch (bytes the kernel must move, floating-point operations counting an FMA as 2, and
+ * issued FP64-pipe instructions for FP64 grids).  Supported classes: CH_K_TSTAGE,
+ * CH_K_WSTAGE, CH_K_MGS, CH_K_RESID1, CH_K_LIM2, CH_K_RHS1, CH_K_RHS2.  Call after an
+ * integration so the workspace holds finite data.  Synchronises.                         */
+ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us,
+                          double *bytes_per_launch, double *flops_per_launch,
+                          double *fp64_instr_per_launch);
 
 /* Message of the last error on the calling thread ("" when none). */
 const char *ch_last_error(void);

@@ -65,6 +65,11 @@ _SIGS = {
     "ch_energy_mass": [_P, _P, _DP, _DP],
     "ch_timing_start": [_P, C.c_int],
     "ch_timing_read": [_P, _DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+    "ch_bench_kernel": [_P, C.c_int, C.c_int, _DP, _DP, _DP, _DP],
+    "ch_create_batch": [C.c_int, C.c_int, C.POINTER(C.c_int64), _DP, C.c_int, C.c_int, _P, C.POINTER(_P)],
+    "ch_destroy_batch": [_P],
+    "ch_batch_layout": [_P, C.POINTER(C.c_int64), _IP],
+    "ch_integrate_batch": [_P, C.POINTER(ch_params), _P, C.POINTER(ch_stats)],
 }
 
 KERNEL_CLASSES = ["prep", "tstage", "wstage", "mgs", "phi", "combine", "rhs1", "rhs2",
@@ -91,6 +96,8 @@ def load():
         L.ch_last_error.argtypes = []
         L.ch_kernel_launches.restype = C.c_int64
         L.ch_kernel_launches.argtypes = [_P]
+        L.ch_batch_kernel_launches.restype = C.c_int64
+        L.ch_batch_kernel_launches.argtypes = [_P]
         _LIB = L
     return _LIB
 
@@ -228,6 +235,14 @@ def ch_timing_start(h, kernel_class):
     _check(load().ch_timing_start(h, k))
 
 
+def ch_bench_kernel(h, kernel_class, reps=200):
+    """Mean launch time (us) and algorithmic bytes / flops / FP64 instructions per launch."""
+    k = KERNEL_CLASSES.index(kernel_class) if isinstance(kernel_class, str) else int(kernel_class)
+    us, b, f, i = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    _check(load().ch_bench_kernel(h, k, reps, C.byref(us), C.byref(b), C.byref(f), C.byref(i)))
+    return {"avg_us": us.value, "bytes": b.value, "flops": f.value, "fp64_instr": i.value}
+
+
 def ch_timing_read(h):
     ms = C.c_double(); n = C.c_int64(); counts = (C.c_int64 * len(KERNEL_CLASSES))()
     _check(load().ch_timing_read(h, C.byref(ms), C.byref(n), counts))
@@ -261,3 +276,39 @@ class Grid:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---- batches --------------------------------------------------------------------------
+def ch_create_batch(dim, sizes, eps, precision=CH_FP64, mmax_capacity=30, stream=None):
+    """sizes: list of per-instance point counts per axis (int for a cube/square)."""
+    count = len(sizes)
+    flat = []
+    for sz in sizes:
+        sz = [int(sz)] * dim if isinstance(sz, (int,)) or hasattr(sz, "__index__") else [int(v) for v in sz]
+        flat += sz + [1] * (3 - dim)
+    arr = (C.c_int64 * (3 * count))(*flat)
+    ep = (C.c_double * count)(*[float(e) for e in eps])
+    h = C.c_void_p()
+    _check(load().ch_create_batch(dim, count, arr, ep, precision, mmax_capacity, _stream(stream), C.byref(h)))
+    return h
+
+
+def ch_destroy_batch(h):
+    _check(load().ch_destroy_batch(h))
+
+
+def ch_batch_layout(h, count):
+    offs = (C.c_int64 * (count + 1))()
+    cl = C.c_int()
+    _check(load().ch_batch_layout(h, offs, C.byref(cl)))
+    return list(offs), cl.value
+
+
+def ch_integrate_batch(h, prm, y, count):
+    st = (ch_stats * count)()
+    _check(load().ch_integrate_batch(h, C.byref(prm), _ptr(y), st))
+    return [s.as_dict() for s in st]
+
+
+def ch_batch_kernel_launches(h):
+    return load().ch_batch_kernel_launches(h)

@@ -7,11 +7,13 @@
 // kernels of an iteration queued after convergence return at once.
 #include <math.h>
 #include <stdarg.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <vector>
 
@@ -29,6 +31,11 @@ static ch_status fail(ch_status st, const char *fmt, ...) {
     vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
     va_end(ap);
     return st;
+}
+
+namespace ch {
+// error message shared by every entry point of the library (ch_last_error)
+void set_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
 }
 
 #define CUDA_TRY(expr)                                                                      \
@@ -50,6 +57,13 @@ struct StepRecord {
     int jexit, restarts, shrunk, p;
 };
 
+// One captured Arnoldi iteration (Fig. 2 lines 4-20 for a fixed j) and what it launches.
+struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+    int64_t counts[CH_K_COUNT] = {0};
+};
+
 struct ch_grid {
     Geom g;
     int precision;
@@ -58,6 +72,9 @@ struct ch_grid {
     Launch L;
     int64_t launches;
     ch::Timing timing;
+    cudaStream_t cap_stream;      // private non-blocking stream used only to capture graphs
+    std::map<std::tuple<int, const void *, int, int>, IterGraph> graphs;
+    int use_graphs;
     // device workspace
     double *D, *G, *t, *q;        // per-step coefficients and stage scratch
     double *F[2];                 // rhs buffers; F[cur] is basis column 0 of a Krylov run
@@ -106,10 +123,6 @@ static ch_status check_launch() {
     return CH_OK;
 }
 
-static double *basis(ch_grid *g, double *slot0, int c) {   // W_c, 1-based
-    return c == 1 ? slot0 : g->V + (int64_t)(c - 2) * g->ldv;
-}
-
 // Fig. 1 step 1 in closed form: column j of A_hat has the entries
 //   centre  d sigma + eps^2 (sigma^2 + 2 sum_a s_a^2),   +-e_a  -s_a (d + 2 eps^2 sigma),
 //   +-2e_a  eps^2 s_a^2,   +-e_a +-e_b  2 eps^2 s_a s_b   (distinct when every n_a >= 4),
@@ -146,39 +159,80 @@ static void rhs(ch_grid *g, const double *y, double *out, int eyre, int mode,
     ch::launch_rhs2(g->L, g->g, g->t, (mode & 2) ? g->q : nullptr, out, y0, f0, y, half_tau, mode);
 }
 
-struct RunResult {
-    int jexit;
-    double tau;
-    int shrunk;
-    int phi_evals;
-};
-
 // One Krylov run of Fig. 2.  Basis column W_1 is in slot0 and red[0] = ||W_1||^2 (and
 // red[1] = ||g_hat||^2 when use_ghat).  Dm must hold the linearisation coefficients in the
 // basis precision VT.  The result y0 + V_j (beta u) is written to ynext (FP64); the run's
 // scalars are left in ctrl (not synchronised).
+// Kernels of Arnoldi iteration j (Fig. 2 lines 4-20) and the copy of the device `active`
+// flag to pinned memory, queued on L.stream.
+template <typename VT>
+static void queue_iteration(ch_grid *g, const Launch &L, VT *slot0, VT *V, const VT *Dm, VT *t,
+                            int j, int mmax, cudaStream_t stream) {
+    const int ldh = g->mmax_cap;
+    auto W = [&](int c) -> VT * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * g->ldv; };
+    VT *Wj = W(j), *Wn = W(j + 1);
+    ch::launch_tstage<VT>(L, g->g, Wj, Dm, t, 1);
+    ch::launch_wstage<VT>(L, g->g, t, Wn, slot0, &g->H[0 * ldh + (j - 1)], j - 1, 1);
+    for (int k = 1; k <= j; ++k) {
+        const int last = (k == j);
+        ch::launch_mgs<VT>(L, g->g.N, Wn, W(k), last ? nullptr : W(k + 1),
+                           &g->H[(k - 1) * ldh + (j - 1)], last ? nullptr : &g->H[k * ldh + (j - 1)],
+                           k, last);
+    }
+    ch::launch_phi(L, g->H, ldh, j, mmax, g->u, g->phi_scratch);
+    cudaMemcpyAsync(&g->hflag[j & 1], &g->ctrl->active, sizeof(int), cudaMemcpyDeviceToHost, stream);
+}
+
+// The iteration as a CUDA graph, captured on the private stream the first time this
+// (precision, start column, j, m_max) occurs and replayed afterwards.
+template <typename VT>
+static ch_status iteration_graph(ch_grid *g, VT *slot0, VT *V, const VT *Dm, VT *t, int j,
+                                 int mmax, IterGraph **out) {
+    auto key = std::make_tuple((int)sizeof(VT), (const void *)slot0, j, mmax);
+    auto it = g->graphs.find(key);
+    if (it != g->graphs.end()) { *out = &it->second; return CH_OK; }
+    IterGraph ig;
+    ch::Timing counter;                       // counts only (cls = -1), no events
+    Launch Lc = g->L;
+    Lc.stream = g->cap_stream;
+    Lc.launches = &ig.launches;
+    Lc.timing = &counter;
+    cudaGraph_t graph;
+    CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+    queue_iteration<VT>(g, Lc, slot0, V, Dm, t, j, mmax, g->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+    if (e != cudaSuccess) return fail(CH_ECUDA, "graph capture of iteration %d: %s", j, cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ig.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(CH_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
+    for (int k = 0; k < CH_K_COUNT; ++k) ig.counts[k] = counter.counts[k];
+    *out = &(g->graphs[key] = ig);
+    return CH_OK;
+}
+
+// One Krylov run of Fig. 2.  Basis column W_1 is in slot0 and red[0] = ||W_1||^2 (and
+// red[1] = ||g_hat||^2 when use_ghat).  Dm must hold the linearisation coefficients in the
+// basis precision VT.  The iteration loop is left with the run's scalars in ctrl; the
+// caller queues the combine.  Iteration j+1 is queued before iteration j's flag is read.
 template <typename VT>
 static ch_status krylov_run_t(ch_grid *g, const double *y0, VT *slot0, VT *V, const VT *Dm,
                               VT *t, double tau0, double tol_phi_fixed, double tol, int use_ghat,
                               int mmax, double *ynext) {
+    (void)y0; (void)ynext;
     const Launch &L = g->L;
-    const int ldh = g->mmax_cap;
-    auto W = [&](int c) -> VT * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * g->ldv; };
     ch::launch_krylov_arm(L, tau0, tol_phi_fixed, tol, use_ghat);
+    const bool graphs = g->use_graphs && g->timing.cls < 0;
     for (int j = 1; j <= mmax; ++j) {
-        VT *Wj = W(j), *Wn = W(j + 1);
-        ch::launch_tstage<VT>(L, g->g, Wj, Dm, t, 1);
-        ch::launch_wstage<VT>(L, g->g, t, Wn, slot0, &g->H[0 * ldh + (j - 1)], j - 1, 1);
-        for (int k = 1; k <= j; ++k) {
-            const int last = (k == j);
-            ch::launch_mgs<VT>(L, g->g.N, Wn, W(k), last ? nullptr : W(k + 1),
-                               &g->H[(k - 1) * ldh + (j - 1)], last ? nullptr : &g->H[k * ldh + (j - 1)],
-                               k, last);
+        if (graphs) {
+            IterGraph *ig;
+            CH_TRY(iteration_graph<VT>(g, slot0, V, Dm, t, j, mmax, &ig));
+            CUDA_TRY(cudaGraphLaunch(ig->exec, g->stream));
+            g->launches += ig->launches;
+            for (int k = 0; k < CH_K_COUNT; ++k) g->timing.counts[k] += ig->counts[k];
+        } else {
+            queue_iteration<VT>(g, L, slot0, V, Dm, t, j, mmax, g->stream);
         }
-        ch::launch_phi(L, g->H, ldh, j, mmax, g->u, g->phi_scratch);
         CH_TRY(check_launch());
-        CUDA_TRY(cudaMemcpyAsync(&g->hflag[j & 1], &g->ctrl->active, sizeof(int),
-                                 cudaMemcpyDeviceToHost, g->stream));
         CUDA_TRY(cudaEventRecord(g->ev[j & 1], g->stream));
         if (j >= 2) {
             CUDA_TRY(cudaEventSynchronize(g->ev[(j - 1) & 1]));
@@ -379,6 +433,94 @@ ch_status ch_timing_start(ch_grid *g, int kernel_class) {
     return CH_OK;
 }
 
+ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us,
+                          double *bytes_per_launch, double *flops_per_launch,
+                          double *fp64_instr_per_launch) {
+    if (!g || reps < 1 || reps > 100000) return fail(CH_EINVAL, "bad arguments");
+    const int d = g->g.dim;
+    const double N = (double)g->g.N;
+    const bool mixed = g->precision == CH_MIXED;
+    const double vb = mixed ? 4.0 : 8.0;           // bytes of one Krylov-vector value
+    double bytes = 0, flops = 0, instr = 0;
+    Launch Lc = g->L;
+    ch::Timing counter;
+    int64_t cnt = 0;
+    Lc.stream = g->cap_stream;
+    Lc.launches = &cnt;
+    Lc.timing = &counter;
+    int one = 1;
+    CUDA_TRY(cudaMemcpyAsync(&g->ctrl->active, &one, sizeof(int), cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    cudaGraph_t graph;
+    CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < reps; ++r) {
+        switch (kernel_class) {
+        case CH_K_TSTAGE:   // t = D x - sum kap (pairs): 1 mul + d (add + fma)
+            if (mixed) ch::launch_tstage<float>(Lc, g->g, g->Wf[0], g->Df, g->tf, 0);
+            else ch::launch_tstage<double>(Lc, g->g, g->F[0], g->D, g->t, 0);
+            bytes = 3 * vb * N; flops = (1 + 3.0 * d) * N; instr = mixed ? 0 : (1 + 2.0 * d) * N;
+            break;
+        case CH_K_WSTAGE:   // w = c0 t - sum c (pairs), dot with v1: 1 mul + d (add + fma) + fma
+            if (mixed) ch::launch_wstage<float>(Lc, g->g, g->tf, g->Vf, g->Wf[0], &g->H[0], 0, 0);
+            else ch::launch_wstage<double>(Lc, g->g, g->t, g->V, g->F[0], &g->H[0], 0, 0);
+            bytes = 3 * vb * N; flops = (3 + 3.0 * d) * N; instr = mixed ? 0 : (2 + 2.0 * d) * N;
+            break;
+        case CH_K_MGS:      // w -= c v_k, dot(w, v_{k+1}): 2 fma
+            if (mixed) ch::launch_mgs<float>(Lc, g->g.N, g->Vf, g->Wf[0], g->Wf[1], &g->H[0], &g->H[1], 1, 0);
+            else ch::launch_mgs<double>(Lc, g->g.N, g->V, g->F[0], g->F[1], &g->H[0], &g->H[1], 1, 0);
+            bytes = 4 * vb * N; flops = 4.0 * N; instr = mixed ? 0 : 2.0 * N;
+            break;
+        case CH_K_RESID1:   // t = G - D x + sum kap (pairs): fma + d (add + fma)
+            ch::launch_resid1(Lc, g->g, g->y[0], g->D, g->G, g->t);
+            bytes = 32.0 * N; flops = (2 + 3.0 * d) * N; instr = (1 + 2.0 * d) * N;
+            break;
+        case CH_K_LIM2:     // r = c0 t - sum c (pairs); fma(ca, prev, fma(alpha, yn, r))
+            ch::launch_lim2(Lc, g->g, g->t, g->y[2], g->y[0], g->y[1], 0.5, 1e-3, 0.9);
+            bytes = 32.0 * N; flops = (5 + 3.0 * d) * N; instr = (3 + 2.0 * d) * N;
+            break;
+        case CH_K_RHS1:     // mu = (y^2 + c) y - sum kap (pairs): fma, mul, d (add + fma)
+            ch::launch_rhs1(Lc, g->g, g->y[2], 0, g->t, nullptr);
+            bytes = 16.0 * N; flops = (3 + 3.0 * d) * N; instr = (2 + 2.0 * d) * N;
+            break;
+        case CH_K_RHS2:     // f = -(sigma mu - sum s (pairs)), ||f||^2
+            ch::launch_rhs2(Lc, g->g, g->t, nullptr, g->y[1], nullptr, nullptr, g->y[2], 0.0, 1);
+            bytes = 16.0 * N; flops = (3 + 3.0 * d) * N; instr = (2 + 2.0 * d) * N;
+            break;
+        default:
+            cudaStreamEndCapture(g->cap_stream, &graph);
+            return fail(CH_EINVAL, "kernel class %d cannot be benchmarked", kernel_class);
+        }
+    }
+    cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+    if (e != cudaSuccess) return fail(CH_ECUDA, "capture: %s", cudaGetErrorString(e));
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(CH_ECUDA, "instantiate: %s", cudaGetErrorString(e));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaGraphLaunch(exec, g->stream));              // warm-up
+    CUDA_TRY(cudaEventRecord(e0, g->stream));
+    CUDA_TRY(cudaGraphLaunch(exec, g->stream));
+    CUDA_TRY(cudaEventRecord(e1, g->stream));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(exec);
+    int zero = 0;
+    CUDA_TRY(cudaMemcpyAsync(&g->ctrl->active, &zero, sizeof(int), cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    g->launches += 2 * cnt;
+    if (avg_us) *avg_us = 1e3 * ms / reps;
+    if (bytes_per_launch) *bytes_per_launch = bytes;
+    if (flops_per_launch) *flops_per_launch = flops;
+    if (fp64_instr_per_launch) *fp64_instr_per_launch = instr;
+    return CH_OK;
+}
+
 ch_status ch_timing_read(ch_grid *g, double *total_ms, int64_t *timed_launches, int64_t *counts) {
     if (!g) return fail(CH_EINVAL, "null grid");
     CUDA_TRY(cudaStreamSynchronize(g->stream));
@@ -429,6 +571,11 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
     g->rec_cap = 0;
     g->resume = 0;
     g->t_last = g->tau_last = 0.0;
+    g->cap_stream = nullptr;
+    {
+        const char *env = getenv("CH_NO_GRAPHS");
+        g->use_graphs = !(env && env[0] == '1');
+    }
 
     auto cleanup_fail = [&](ch_status st, const char *what, cudaError_t e) {
         ch_destroy_grid(g);
@@ -439,7 +586,7 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cleanup_fail(CH_ECUDA, "device query", e);
     const int64_t want = (N + ch::kThreads - 1) / ch::kThreads;
-    g->L.blocks = (int)std::min<int64_t>(want, (int64_t)sms * 8);
+    g->L.blocks = (int)std::min<int64_t>(want, (int64_t)sms * ch::kBlocksPerSM);
     g->L.stream = g->stream;
     g->L.launches = &g->launches;
     g->L.timing = &g->timing;
@@ -478,6 +625,7 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
     if (e == cudaSuccess) e = cudaMallocHost((void **)&g->hflag, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = (cudaError_t)ch::phi_setup();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cleanup_fail(CH_ECUDA, "grid set-up", e);
@@ -503,6 +651,8 @@ ch_status ch_destroy_grid(ch_grid *g) {
     if (g->ev[0]) cudaEventDestroy(g->ev[0]);
     if (g->ev[1]) cudaEventDestroy(g->ev[1]);
     for (auto &e : g->timing.ev) if (e) cudaEventDestroy(e);
+    for (auto &kv : g->graphs) if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
     return CH_OK;
 }

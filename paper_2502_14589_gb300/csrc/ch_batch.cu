@@ -1,0 +1,840 @@
+// ch_batch.cu -- many independent Cahn-Hilliard instances (uneven sizes, own eps, own time,
+// own adaptive step and Krylov state) advanced together with adaptive EE2 (Fig. 4).
+//
+// Layout in HBM: the instances' vectors are concatenated, instance i at [off_i, off_i + N_i)
+// with off_{i+1} = off_i + N_i rounded up to 64 values.  Every kernel runs over a table of
+// chunks (instance, local range); the chunk length is picked at creation by timing a stencil
+// pass for a few candidates.  Reductions close per instance: each chunk writes its partial,
+// and the last chunk of an instance to arrive (per-instance arrival counter) sums that
+// instance's partials in chunk order, so results do not depend on scheduling.  Each
+// instance has its own control block (Ctrl), Hessenberg matrix and step state; the
+// projected phi runs as one 8-CTA cluster per instance, and the step controller of Fig. 4
+// runs on the device.  The host only polls "any Krylov run active" per Arnoldi iteration
+// and "any instance before T" per step.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "ch_internal.cuh"
+
+namespace ch {
+void set_error(const char *msg);
+}
+
+namespace {
+
+using ch::Ctrl;
+using ch::Launch;
+using ch::LaunchScope;
+using ch::kThreads;
+
+struct Inst {
+    int n[3];
+    int dim;
+    int64_t off, N;
+    double s[3], kap[3], sigma, eps2;
+    int first_chunk, nchunks;
+};
+
+struct Chunk {
+    int inst;
+    int begin, end;      // local index range of the instance
+    int pad;
+};
+
+// Per-instance step state (Fig. 4 steps 1-10) and counters.
+struct BState {
+    double t, tau, est;
+    int done, clipped, status, pad;
+    long long steps, matvecs, rhs_evals, krylov_iters, tau_shrinks, phi_evals;
+};
+
+ch_status bfail(ch_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ch::set_error(buf);
+    return st;
+}
+
+#define BCUDA(expr)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return bfail(CH_ECUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),  \
+                         __FILE__, __LINE__);                                               \
+    } while (0)
+#define BTRY(expr)                  \
+    do {                            \
+        ch_status s_ = (expr);      \
+        if (s_ != CH_OK) return s_; \
+    } while (0)
+
+__device__ __forceinline__ unsigned bnp(unsigned i, unsigned c, unsigned n, unsigned st) {
+    return (c + 1u == n) ? i - (n - 1u) * st : i + st;
+}
+__device__ __forceinline__ unsigned bnm(unsigned i, unsigned c, unsigned n, unsigned st) {
+    return (c == 0u) ? i + (n - 1u) * st : i - st;
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ void pair_sums_inst(const Inst &I, const T *__restrict__ x, unsigned l,
+                                               T (&ps)[3]) {
+    const unsigned n0 = (unsigned)I.n[0], n1 = (unsigned)I.n[1];
+    const unsigned c0 = l % n0, r = l / n0, c1 = r % n1;
+    ps[0] = x[bnp(l, c0, n0, 1u)] + x[bnm(l, c0, n0, 1u)];
+    ps[1] = x[bnp(l, c1, n1, n0)] + x[bnm(l, c1, n1, n0)];
+    if (DIM == 3) {
+        const unsigned n2 = (unsigned)I.n[2], s2 = n0 * n1, c2 = r / n1;
+        ps[2] = x[bnp(l, c2, n2, s2)] + x[bnm(l, c2, n2, s2)];
+    } else {
+        ps[2] = T(0);
+    }
+}
+
+template <typename VT> struct BDot;
+template <> struct BDot<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct BDot<float> {     // exact products, compensated FP32 sum (as ch_stencil.cu)
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Per-instance reduction: chunk partials, then the instance's last chunk sums them in order.
+template <int K, typename Fin>
+__device__ __forceinline__ void inst_sum(double (&v)[K], const Inst &I, int inst, double *partials,
+                                         int nchunks_total, unsigned int *tickets, Fin fin) {
+    __shared__ bool last;
+    ch::block_sum<K>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) partials[(size_t)k * nchunks_total + blockIdx.x] = v[k];
+        __threadfence();
+        last = (atomicAdd(&tickets[inst], 1u) == (unsigned)I.nchunks - 1u);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        acc[k] = 0.0;
+        for (int c = threadIdx.x; c < I.nchunks; c += blockDim.x)
+            acc[k] += __ldcg(&partials[(size_t)k * nchunks_total + I.first_chunk + c]);
+    }
+    ch::block_sum<K>(acc);
+    if (threadIdx.x == 0) {
+        fin(acc);
+        tickets[inst] = 0u;
+    }
+}
+
+#define CHUNK_BEGIN                                        \
+    const Chunk ck = chunks[blockIdx.x];                   \
+    const Inst I = insts[ck.inst];
+
+#define CHUNK_LOOP(l) for (unsigned l = ck.begin + threadIdx.x; l < (unsigned)ck.end; l += blockDim.x)
+
+// ---- per-step coefficients: D = 3y^2 - 1 + eps^2 sigma (in the basis precision) -----------
+template <typename VT>
+__global__ void __launch_bounds__(kThreads)
+kb_prep(const Inst *insts, const Chunk *chunks, const BState *bs, const double *__restrict__ y,
+        VT *__restrict__ D) {
+    CHUNK_BEGIN
+    if (bs[ck.inst].done) return;
+    const double dconst = -1.0 + I.eps2 * I.sigma;
+    CHUNK_LOOP(l) {
+        const double yi = y[I.off + l];
+        D[I.off + l] = (VT)fma(3.0, yi * yi, dconst);
+    }
+}
+
+// ---- f(y) of Eq. (IVP), FP64; stage 1 ------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+kb_rhs1(const Inst *insts, const Chunk *chunks, const BState *bs, const double *__restrict__ y,
+        double *__restrict__ mu, double *__restrict__ q) {
+    CHUNK_BEGIN
+    if (bs[ck.inst].done) return;
+    const double *yi_ = y + I.off;
+    const double cshift = I.eps2 * I.sigma - 1.0;
+    CHUNK_LOOP(l) {
+        double ps[3];
+        pair_sums_inst<DIM>(I, yi_, l, ps);
+        const double yi = yi_[l];
+        const double y2 = yi * yi;
+        double m = (y2 + cshift) * yi;
+        m = fma(-I.kap[0], ps[0], m);
+        m = fma(-I.kap[1], ps[1], m);
+        if (DIM == 3) m = fma(-I.kap[2], ps[2], m);
+        mu[I.off + l] = m;
+        q[I.off + l] = 2.0 * y2 * yi;
+    }
+}
+
+// stage 2: f (FP64 and basis precision), ||f||^2, ||g_hat||^2 and, with `est`, the sums of
+// Eq. (LIMest) for the step the instance's Krylov run took (ctrl->tau).
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kThreads)
+kb_rhs2(const Inst *insts, const Chunk *chunks, const BState *bs, Ctrl *ctrls,
+        const double *__restrict__ mu, const double *__restrict__ q, double *__restrict__ f,
+        VT *__restrict__ fvt, const double *__restrict__ y0, const double *__restrict__ f0,
+        const double *__restrict__ y1, int est, double *partials, int nct, unsigned int *tickets) {
+    CHUNK_BEGIN
+    if (bs[ck.inst].done) return;
+    const double *mu_ = mu + I.off, *q_ = q + I.off;
+    const double half_tau = 0.5 * ctrls[ck.inst].tau;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    CHUNK_LOOP(l) {
+        double ps[3], qs[3];
+        pair_sums_inst<DIM>(I, mu_, l, ps);
+        double r = -I.sigma * mu_[l];
+        r = fma(I.s[0], ps[0], r);
+        r = fma(I.s[1], ps[1], r);
+        if (DIM == 3) r = fma(I.s[2], ps[2], r);
+        const int64_t gi = I.off + l;
+        f[gi] = r;
+        if (fvt) fvt[gi] = (VT)r;
+        acc[0] = fma(r, r, acc[0]);
+        pair_sums_inst<DIM>(I, q_, l, qs);
+        double gh = I.sigma * q_[l];
+        gh = fma(-I.s[0], qs[0], gh);
+        gh = fma(-I.s[1], qs[1], gh);
+        if (DIM == 3) gh = fma(-I.s[2], qs[2], gh);
+        acc[1] = fma(gh, gh, acc[1]);
+        if (est) {
+            const double ypc = fma(half_tau, f0[gi] + r, y0[gi]);
+            const double d = y1[gi] - ypc;
+            acc[2] = fma(d, d, acc[2]);
+            acc[3] = fma(ypc, ypc, acc[3]);
+        }
+    }
+    Ctrl *ctrl = ctrls + ck.inst;
+    inst_sum<4>(acc, I, ck.inst, partials, nct, tickets, [&](double (&tot)[4]) {
+        for (int k = 0; k < 4; ++k) ctrl->red[k] = tot[k];
+    });
+}
+
+// ---- Krylov start of every instance still before T: Fig. 4 steps 3-5 and Fig. 2 line 2 --
+__global__ void kb_arm(Ctrl *ctrls, BState *bs, int count, double T, double tol_phi_fixed,
+                       double tol) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    Ctrl *c = ctrls + i;
+    BState *b = bs + i;
+    c->jexit = 0; c->converged = 0; c->shrunk = 0; c->phi_evals = 0;
+    c->hnext2 = 0.0; c->resnorm = 0.0;
+    if (b->done) { c->active = 0; return; }
+    b->clipped = 0;
+    if (b->t + b->tau > T) { b->tau = T - b->t; b->clipped = 1; }
+    const double beta = sqrt(c->red[0]);
+    c->beta = beta;
+    c->tau0 = b->tau;
+    c->tau = b->tau;
+    double tp = tol_phi_fixed;
+    if (!(tp > 0.0)) {                                       // Eq. (tol_phi)
+        const double a = sqrt(c->red[1]) / (10.0 * beta);
+        double m = a < 0.1 ? a : 0.1;
+        if (10.0 * tol < m) m = 10.0 * tol;
+        tp = m > 1e-7 ? m : 1e-7;
+    }
+    c->tol_phi = tp;
+    if (!isfinite(beta)) { c->status = CH_ENONFINITE; c->active = 0; return; }
+    c->active = beta > 0.0 ? 1 : 0;
+    c->gam[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+// ---- Arnoldi iteration (Fig. 2 lines 4-9), per chunk of the still-active instances --------
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kThreads)
+kb_tstage(const Inst *insts, const Chunk *chunks, const Ctrl *ctrls, const VT *__restrict__ x,
+          const VT *__restrict__ D, VT *__restrict__ t) {
+    CHUNK_BEGIN
+    if (!ctrls[ck.inst].active) return;
+    const VT *xi = x + I.off;
+    const VT k0 = (VT)I.kap[0], k1 = (VT)I.kap[1], k2 = (VT)I.kap[2];
+    CHUNK_LOOP(l) {
+        VT ps[3];
+        pair_sums_inst<DIM>(I, xi, l, ps);
+        VT acc = D[I.off + l] * xi[l];
+        acc = fma(-k0, ps[0], acc);
+        acc = fma(-k1, ps[1], acc);
+        if (DIM == 3) acc = fma(-k2, ps[2], acc);
+        t[I.off + l] = acc;
+    }
+}
+
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kThreads)
+kb_wstage(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, const VT *__restrict__ t,
+          VT *__restrict__ w, const VT *__restrict__ v1, double *Hs, int64_t hstride, int ldh,
+          int j, double *partials, int nct, unsigned int *tickets) {
+    CHUNK_BEGIN
+    Ctrl *ctrl = ctrls + ck.inst;
+    if (!ctrl->active) return;
+    const double gam = ctrl->gam[j - 1];
+    const VT c0 = (VT)(gam * I.sigma), c1 = (VT)(gam * I.s[0]), c2 = (VT)(gam * I.s[1]),
+             c3 = (VT)(gam * I.s[2]);
+    const VT *ti = t + I.off;
+    BDot<VT> acc;
+    CHUNK_LOOP(l) {
+        VT ps[3];
+        pair_sums_inst<DIM>(I, ti, l, ps);
+        VT r = c0 * ti[l];
+        r = fma(-c1, ps[0], r);
+        r = fma(-c2, ps[1], r);
+        if (DIM == 3) r = fma(-c3, ps[2], r);
+        w[I.off + l] = r;
+        acc.add(r, v1[I.off + l]);
+    }
+    double v[1] = {acc.value()};
+    double *H = Hs + ck.inst * hstride;
+    inst_sum<1>(v, I, ck.inst, partials, nct, tickets,
+                [&](double (&tot)[1]) { H[0 * ldh + (j - 1)] = ctrl->gam[0] * tot[0]; });
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads)
+kb_mgs(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, VT *__restrict__ w,
+       const VT *__restrict__ vk, const VT *__restrict__ vk1, double *Hs, int64_t hstride,
+       int ldh, int j, int k, int last, double *partials, int nct, unsigned int *tickets) {
+    CHUNK_BEGIN
+    Ctrl *ctrl = ctrls + ck.inst;
+    if (!ctrl->active) return;
+    double *H = Hs + ck.inst * hstride;
+    const VT c = (VT)(H[(k - 1) * ldh + (j - 1)] * ctrl->gam[k - 1]);
+    BDot<VT> acc;
+    if (!last) {
+        CHUNK_LOOP(l) {
+            const int64_t gi = I.off + l;
+            const VT r = fma(-c, vk[gi], w[gi]);
+            w[gi] = r;
+            acc.add(r, vk1[gi]);
+        }
+        double v[1] = {acc.value()};
+        inst_sum<1>(v, I, ck.inst, partials, nct, tickets,
+                    [&](double (&tot)[1]) { H[k * ldh + (j - 1)] = ctrl->gam[k] * tot[0]; });
+    } else {
+        CHUNK_LOOP(l) {
+            const int64_t gi = I.off + l;
+            const VT r = fma(-c, vk[gi], w[gi]);
+            w[gi] = r;
+            acc.add(r, r);
+        }
+        double v[1] = {acc.value()};
+        inst_sum<1>(v, I, ck.inst, partials, nct, tickets,
+                    [&](double (&tot)[1]) { ctrl->hnext2 = tot[0]; });
+    }
+}
+
+// 1 in *flag when some instance's Krylov run is still active.
+__global__ void kb_any(const Ctrl *ctrls, int count, int *flag) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < count; i += blockDim.x)
+        if (ctrls[i].active) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = any;
+}
+
+// ---- Fig. 2 line 23 per instance; finished instances carry y over -------------------------
+template <typename VT>
+__global__ void __launch_bounds__(kThreads)
+kb_combine(const Inst *insts, const Chunk *chunks, const BState *bs, Ctrl *ctrls,
+           const double *__restrict__ y0, const VT *__restrict__ v0, const VT *__restrict__ V,
+           int64_t ldv, double *__restrict__ ynext, float *__restrict__ dtmp, double *partials,
+           int nct, unsigned int *tickets) {
+    CHUNK_BEGIN
+    Ctrl *ctrl = ctrls + ck.inst;
+    const int j = bs[ck.inst].done ? 0 : ctrl->jexit;
+    __shared__ double coef[130];
+    for (int c = threadIdx.x; c < j; c += blockDim.x) coef[c] = ctrl->coef[c];
+    __syncthreads();
+    if (sizeof(VT) == 8) {
+        CHUNK_LOOP(l) {
+            const int64_t gi = I.off + l;
+            double acc = 0.0;
+            if (j > 0) acc = coef[0] * (double)v0[gi];
+            for (int c = 1; c < j; ++c) acc = fma(coef[c], (double)V[(c - 1) * ldv + gi], acc);
+            ynext[gi] = y0[gi] + acc;
+        }
+    } else {                           // mixed: FP32 increment, its mass removed in pass b
+        BDot<float> m;
+        CHUNK_LOOP(l) {
+            const int64_t gi = I.off + l;
+            float a = 0.f;
+            if (j > 0) a = (float)coef[0] * (float)v0[gi];
+            for (int c = 1; c < j; ++c) a = fmaf((float)coef[c], (float)V[(c - 1) * ldv + gi], a);
+            dtmp[gi] = a;
+            m.add(a, 1.0f);
+        }
+        double v[1] = {m.value()};
+        inst_sum<1>(v, I, ck.inst, partials, nct, tickets,
+                    [&](double (&tot)[1]) { ctrl->red[6] = tot[0]; });
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+kb_combine32b(const Inst *insts, const Chunk *chunks, const BState *bs, const Ctrl *ctrls,
+              const double *__restrict__ y0, const float *__restrict__ d,
+              double *__restrict__ ynext) {
+    CHUNK_BEGIN
+    const bool moved = !bs[ck.inst].done && ctrls[ck.inst].jexit > 0;
+    const double mean = moved ? ctrls[ck.inst].red[6] / (double)I.N : 0.0;
+    CHUNK_LOOP(l) {
+        const int64_t gi = I.off + l;
+        ynext[gi] = moved ? y0[gi] + ((double)d[gi] - mean) : y0[gi];
+    }
+}
+
+// ---- Fig. 4 steps 8-10 per instance: est, time, next step size (Eq. EEdt), counters -------
+__global__ void kb_control(Ctrl *ctrls, BState *bs, int count, double T, double tol,
+                           int *remaining) {
+    __shared__ int rem;
+    if (threadIdx.x == 0) rem = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        Ctrl *c = ctrls + i;
+        BState *b = bs + i;
+        if (!b->done) {
+            if (c->status != 0) {
+                b->status = c->status;
+                b->done = 1;
+            } else {
+                const double taken = c->tau;
+                const double est = sqrt(c->red[2]) / sqrt(c->red[3]);
+                b->est = est;
+                b->matvecs += 1 + c->jexit;
+                b->krylov_iters += c->jexit;
+                b->tau_shrinks += c->shrunk;
+                b->phi_evals += c->phi_evals;
+                b->rhs_evals += 1;
+                b->steps += 1;
+                b->t = (b->clipped && taken == b->tau) ? T : b->t + taken;
+                const double grow = 1.25 * taken;
+                b->tau = (est > 0.0) ? fmin(grow, sqrt(tol / est) * taken) : grow;
+                if (!isfinite(est)) { b->status = CH_ENONFINITE; b->done = 1; }
+                else if (!(b->t < T)) b->done = 1;
+                else if (!(b->tau > 0.0) || b->t + b->tau == b->t) { b->status = CH_ENOTCONV; b->done = 1; }
+            }
+        }
+        if (!b->done) atomicAdd(&rem, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *remaining = rem;
+}
+
+__global__ void kb_init(BState *bs, Ctrl *ctrls, int count, double tau0) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    BState b;
+    memset(&b, 0, sizeof b);
+    b.tau = tau0;
+    bs[i] = b;
+    ctrls[i].status = 0;
+    ctrls[i].active = 0;
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------------------------------
+// host side
+// -------------------------------------------------------------------------------------------
+struct ch_batch {
+    int dim, count, precision, mmax_cap, nchunks, chunk_len;
+    int64_t Ntot;
+    cudaStream_t stream, cap_stream;
+    std::vector<Inst> hinst;
+    std::vector<int64_t> offsets;
+    Inst *insts;
+    Chunk *chunks;
+    BState *bs;
+    Ctrl *ctrls;
+    double *H, *u;           // count x (mmax+1) x mmax, count x (mmax+1)
+    double *ynew, *F[2], *mu, *q, *partials;
+    unsigned int *tickets;
+    void *D, *t, *V, *W[2];  // basis precision
+    int *dflags;             // [0] any active, [1] remaining
+    int *hflags;             // pinned: [0],[1] any active (alternating), [2] remaining
+    cudaEvent_t ev[2];
+    int64_t launches;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (slot, j) -> iteration graph
+    int mmax_graphs;
+};
+
+namespace {
+
+template <typename VT> struct Kern;
+
+Launch make_launch(ch_batch *b, cudaStream_t s) {
+    Launch L;
+    L.blocks = b->nchunks;
+    L.stream = s;
+    L.partials = b->partials;
+    L.ctrl = b->ctrls;
+    L.launches = &b->launches;
+    L.timing = nullptr;
+    return L;
+}
+
+#define BLAUNCH(KERNEL, ...)                                                               \
+    do {                                                                                   \
+        if (b->dim == 3) KERNEL<3><<<b->nchunks, kThreads, 0, s>>>(__VA_ARGS__);           \
+        else KERNEL<2><<<b->nchunks, kThreads, 0, s>>>(__VA_ARGS__);                       \
+        ++b->launches;                                                                     \
+    } while (0)
+#define BLAUNCH_T(KERNEL, VT, ...)                                                         \
+    do {                                                                                   \
+        if (b->dim == 3) KERNEL<3, VT><<<b->nchunks, kThreads, 0, s>>>(__VA_ARGS__);       \
+        else KERNEL<2, VT><<<b->nchunks, kThreads, 0, s>>>(__VA_ARGS__);                   \
+        ++b->launches;                                                                     \
+    } while (0)
+
+template <typename VT>
+void rhs_b(ch_batch *b, cudaStream_t s, const double *y, int slot, int est, const double *y0,
+           const double *f0) {
+    VT *fvt = sizeof(VT) == 8 ? nullptr : (VT *)b->W[slot];
+    BLAUNCH(kb_rhs1, b->insts, b->chunks, b->bs, y, b->mu, b->q);
+    BLAUNCH_T(kb_rhs2, VT, b->insts, b->chunks, b->bs, b->ctrls, b->mu, b->q, b->F[slot], fvt,
+              y0, f0, y, est, b->partials, b->nchunks, b->tickets);
+}
+
+template <typename VT>
+VT *basis_col(ch_batch *b, int slot, int c) {   // W_c, 1-based
+    if (c == 1) return sizeof(VT) == 8 ? (VT *)b->F[slot] : (VT *)b->W[slot];
+    return (VT *)b->V + (int64_t)(c - 2) * b->Ntot;
+}
+
+template <typename VT>
+void queue_iteration_b(ch_batch *b, cudaStream_t s, int slot, int j, int mmax) {
+    const int ldh = b->mmax_cap;
+    const int64_t hs = (int64_t)(b->mmax_cap + 1) * b->mmax_cap;
+    VT *Wj = basis_col<VT>(b, slot, j), *Wn = basis_col<VT>(b, slot, j + 1), *v1 = basis_col<VT>(b, slot, 1);
+    BLAUNCH_T(kb_tstage, VT, b->insts, b->chunks, b->ctrls, Wj, (const VT *)b->D, (VT *)b->t);
+    BLAUNCH_T(kb_wstage, VT, b->insts, b->chunks, b->ctrls, (const VT *)b->t, Wn, v1, b->H, hs, ldh,
+              j, b->partials, b->nchunks, b->tickets);
+    for (int k = 1; k <= j; ++k) {
+        const int last = k == j;
+        kb_mgs<VT><<<b->nchunks, kThreads, 0, s>>>(b->insts, b->chunks, b->ctrls, Wn,
+                                                    basis_col<VT>(b, slot, k),
+                                                    last ? nullptr : basis_col<VT>(b, slot, k + 1),
+                                                    b->H, hs, ldh, j, k, last, b->partials,
+                                                    b->nchunks, b->tickets);
+        ++b->launches;
+    }
+    Launch L = make_launch(b, s);
+    ch::launch_phi_batch(L, b->ctrls, b->H, hs, b->u, b->mmax_cap + 1, ldh, j, mmax, b->count);
+    kb_any<<<1, 256, 0, s>>>(b->ctrls, b->count, &b->dflags[0]);
+    ++b->launches;
+    cudaMemcpyAsync(&b->hflags[j & 1], &b->dflags[0], sizeof(int), cudaMemcpyDeviceToHost, s);
+}
+
+template <typename VT>
+ch_status krylov_b(ch_batch *b, int slot, int mmax, bool use_graphs) {
+    for (int j = 1; j <= mmax; ++j) {
+        if (use_graphs) {
+            auto key = std::make_pair(slot, j);
+            auto it = b->graphs.find(key);
+            cudaGraphExec_t exec;
+            if (it == b->graphs.end()) {
+                cudaGraph_t g;
+                int64_t before = b->launches;
+                BCUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+                queue_iteration_b<VT>(b, b->cap_stream, slot, j, mmax);
+                BCUDA(cudaStreamEndCapture(b->cap_stream, &g));
+                cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return bfail(CH_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
+                b->launches = before;
+                b->graphs[key] = exec;
+            } else {
+                exec = it->second;
+            }
+            BCUDA(cudaGraphLaunch(exec, b->stream));
+            b->launches += 3 + j + 1;
+        } else {
+            queue_iteration_b<VT>(b, b->stream, slot, j, mmax);
+        }
+        BCUDA(cudaGetLastError());
+        BCUDA(cudaEventRecord(b->ev[j & 1], b->stream));
+        if (j >= 2) {
+            BCUDA(cudaEventSynchronize(b->ev[(j - 1) & 1]));
+            if (b->hflags[(j - 1) & 1] == 0) break;
+        }
+    }
+    return CH_OK;
+}
+
+template <typename VT>
+ch_status integrate_b(ch_batch *b, const ch_params *prm, double *y, ch_stats *stats) {
+    cudaStream_t s = b->stream;
+    if (b->mmax_graphs != prm->mmax) {       // graphs bake m_max into the phi step
+        for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+        b->graphs.clear();
+        b->mmax_graphs = prm->mmax;
+    }
+    const bool use_graphs = true;
+    kb_init<<<(b->count + 255) / 256, 256, 0, s>>>(b->bs, b->ctrls, b->count, prm->tau0);
+    double *ycur = y, *ynew = b->ynew;
+    int cur = 0;
+    rhs_b<VT>(b, s, ycur, cur, 0, nullptr, nullptr);                 // f(y^0), norms
+    BCUDA(cudaGetLastError());
+    int64_t steps = 0;
+    for (;;) {
+        kb_arm<<<(b->count + 255) / 256, 256, 0, s>>>(b->ctrls, b->bs, b->count, prm->T,
+                                                      prm->tol_phi, prm->tol);
+        kb_prep<VT><<<b->nchunks, kThreads, 0, s>>>(b->insts, b->chunks, b->bs, ycur, (VT *)b->D);
+        ++b->launches;
+        BTRY(krylov_b<VT>(b, cur, prm->mmax, use_graphs));
+        kb_combine<VT><<<b->nchunks, kThreads, 0, s>>>(
+            b->insts, b->chunks, b->bs, b->ctrls, ycur, basis_col<VT>(b, cur, 1), (VT *)b->V,
+            b->Ntot, ynew, (float *)b->t, b->partials, b->nchunks, b->tickets);
+        if (sizeof(VT) == 4)
+            kb_combine32b<<<b->nchunks, kThreads, 0, s>>>(b->insts, b->chunks, b->bs, b->ctrls,
+                                                           ycur, (float *)b->t, ynew);
+        rhs_b<VT>(b, s, ynew, 1 - cur, 1, ycur, b->F[cur]);           // est, f(y^{n+1})
+        kb_control<<<1, 256, 0, s>>>(b->ctrls, b->bs, b->count, prm->T, prm->tol, &b->dflags[1]);
+        BCUDA(cudaGetLastError());
+        BCUDA(cudaMemcpyAsync(&b->hflags[2], &b->dflags[1], sizeof(int), cudaMemcpyDeviceToHost, s));
+        BCUDA(cudaStreamSynchronize(s));
+        std::swap(ycur, ynew);
+        cur = 1 - cur;
+        ++steps;
+        if (b->hflags[2] == 0) break;
+        if (steps >= prm->max_steps) return bfail(CH_ENOTCONV, "max_steps reached before T");
+    }
+    if (ycur != y) BCUDA(cudaMemcpyAsync(y, ycur, b->Ntot * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    std::vector<BState> hb(b->count);
+    BCUDA(cudaMemcpyAsync(hb.data(), b->bs, b->count * sizeof(BState), cudaMemcpyDeviceToHost, s));
+    BCUDA(cudaStreamSynchronize(s));
+    ch_status rc = CH_OK;
+    for (int i = 0; i < b->count; ++i) {
+        if (hb[i].status && rc == CH_OK)
+            rc = bfail((ch_status)hb[i].status, "instance %d failed (status %d) at t = %g", i, hb[i].status, hb[i].t);
+        if (stats) {
+            ch_stats &st = stats[i];
+            memset(&st, 0, sizeof st);
+            st.steps = hb[i].steps; st.matvecs = hb[i].matvecs; st.rhs_evals = hb[i].rhs_evals;
+            st.krylov_iters = hb[i].krylov_iters; st.tau_shrinks = hb[i].tau_shrinks;
+            st.phi_evals = hb[i].phi_evals; st.t = hb[i].t; st.tau_next = hb[i].tau;
+            st.last_est = hb[i].est;
+        }
+    }
+    return rc;
+}
+
+// Chunk length candidates for the autotuner (values per chunk; a chunk is one thread block).
+const int kChunkCandidates[] = {1024, 2048, 4096, 8192};
+
+void build_chunks(ch_batch *b, int chunk_len, std::vector<Chunk> &ch) {
+    ch.clear();
+    for (int i = 0; i < b->count; ++i) {
+        Inst &I = b->hinst[i];
+        I.first_chunk = (int)ch.size();
+        for (int64_t l = 0; l < I.N; l += chunk_len)
+            ch.push_back(Chunk{i, (int)l, (int)std::min<int64_t>(I.N, l + chunk_len), 0});
+        I.nchunks = (int)ch.size() - I.first_chunk;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+ch_status ch_destroy_batch(ch_batch *b) {
+    if (!b) return CH_OK;
+    cudaStreamSynchronize(b->stream);
+    void *bufs[] = {b->insts, b->chunks, b->bs, b->ctrls, b->H, b->u, b->ynew, b->F[0], b->F[1],
+                    b->mu, b->q, b->partials, b->tickets, b->D, b->t, b->V, b->W[0], b->W[1],
+                    b->dflags};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (b->hflags) cudaFreeHost(b->hflags);
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    if (b->ev[0]) cudaEventDestroy(b->ev[0]);
+    if (b->ev[1]) cudaEventDestroy(b->ev[1]);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
+    return CH_OK;
+}
+
+ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *eps, int precision,
+                          int mmax_capacity, void *cuda_stream, ch_batch **out) {
+    if (!out || !n || !eps) return bfail(CH_EINVAL, "null argument");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return bfail(CH_EINVAL, "dim must be 2 or 3");
+    if (count < 1 || count > 65536) return bfail(CH_EINVAL, "count must be in [1, 65536]");
+    if (precision != CH_FP64 && precision != CH_MIXED) return bfail(CH_EINVAL, "unknown precision");
+    if (mmax_capacity < 1 || mmax_capacity > 63)
+        return bfail(CH_EINVAL, "batch mmax_capacity must be in [1, 63]");
+    ch_batch *b = new ch_batch();
+    b->dim = dim; b->count = count; b->precision = precision; b->mmax_cap = mmax_capacity;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->launches = 0;
+    b->mmax_graphs = -1;
+    b->hinst.resize(count);
+    b->offsets.resize(count + 1);
+    int64_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        Inst &I = b->hinst[i];
+        memset(&I, 0, sizeof I);
+        I.dim = dim;
+        int64_t N = 1;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t na = a < dim ? n[3 * i + a] : 1;
+            if (a < dim && (na < 4 || na > (1 << 20))) { delete b; return bfail(CH_EINVAL, "instance %d: n[%d] out of range [4, 2^20]", i, a); }
+            I.n[a] = (int)na;
+            N *= na;
+        }
+        if (!(eps[i] > 0.0) || !isfinite(eps[i])) { delete b; return bfail(CH_EINVAL, "instance %d: eps must be > 0", i); }
+        I.N = N;
+        I.off = off;
+        I.eps2 = eps[i] * eps[i];
+        I.sigma = 0.0;
+        for (int a = 0; a < dim; ++a) {
+            I.s[a] = (double)I.n[a] * (double)I.n[a];
+            I.kap[a] = I.eps2 * I.s[a];
+            I.sigma += 2.0 * I.s[a];
+        }
+        b->offsets[i] = off;
+        off += (N + 63) / 64 * 64;
+    }
+    b->offsets[count] = off;
+    b->Ntot = off;
+    if (off >= ((int64_t)1 << 31)) { delete b; return bfail(CH_EINVAL, "batch of %lld values exceeds 2^31 - 1", (long long)off); }
+    auto cleanup = [&](const char *what, cudaError_t e) {
+        ch_destroy_batch(b);
+        return bfail(CH_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    };
+    const size_t vb = (size_t)off * sizeof(double);
+    const size_t eb = (size_t)off * (precision == CH_MIXED ? sizeof(float) : sizeof(double));
+    // chunk table for the largest candidate count (most chunks)
+    std::vector<Chunk> ch;
+    build_chunks(b, kChunkCandidates[0], ch);
+    const int max_chunks = (int)ch.size();
+    struct { void **p; size_t bytes; } allocs[] = {
+        {(void **)&b->insts, sizeof(Inst) * count}, {(void **)&b->chunks, sizeof(Chunk) * max_chunks},
+        {(void **)&b->bs, sizeof(BState) * count}, {(void **)&b->ctrls, sizeof(Ctrl) * count},
+        {(void **)&b->H, sizeof(double) * count * (size_t)(mmax_capacity + 1) * mmax_capacity},
+        {(void **)&b->u, sizeof(double) * count * (size_t)(mmax_capacity + 1)},
+        {(void **)&b->ynew, vb}, {(void **)&b->F[0], vb}, {(void **)&b->F[1], vb},
+        {(void **)&b->mu, vb}, {(void **)&b->q, vb},
+        {(void **)&b->partials, sizeof(double) * 4 * (size_t)max_chunks},
+        {(void **)&b->tickets, sizeof(unsigned int) * count},
+        {(void **)&b->D, eb}, {(void **)&b->t, std::max(eb, (size_t)off * sizeof(float))},
+        {(void **)&b->V, eb * (size_t)mmax_capacity}, {(void **)&b->dflags, 2 * sizeof(int)},
+    };
+    for (auto &a : allocs) {
+        cudaError_t e = cudaMalloc(a.p, a.bytes);
+        if (e != cudaSuccess) { cudaGetLastError(); return cleanup("cudaMalloc of batch workspace", e); }
+    }
+    if (precision == CH_MIXED) {
+        for (int k = 0; k < 2; ++k) {
+            cudaError_t e = cudaMalloc(&b->W[k], eb);
+            if (e != cudaSuccess) { cudaGetLastError(); return cleanup("cudaMalloc of FP32 start vectors", e); }
+        }
+    }
+    cudaError_t e = cudaMemset(b->tickets, 0, sizeof(unsigned int) * count);
+    if (e == cudaSuccess) e = cudaMemset(b->ctrls, 0, sizeof(Ctrl) * count);
+    if (e == cudaSuccess) e = cudaMemset(b->H, 0, sizeof(double) * count * (size_t)(mmax_capacity + 1) * mmax_capacity);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->hflags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = (cudaError_t)ch::phi_setup();
+    if (e != cudaSuccess) return cleanup("batch set-up", e);
+    // ---- chunk-length autotuner: time one stencil pass over the whole batch per candidate
+    {
+        int one = 1;
+        for (int i = 0; i < count; ++i)
+            cudaMemcpy(&b->ctrls[i].active, &one, sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemset(b->D, 0, eb);
+        cudaMemset(b->F[0], 0, vb);
+        if (precision == CH_MIXED) cudaMemset(b->W[0], 0, eb);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best_ms = 1e30f;
+        int best = kChunkCandidates[0];
+        for (int cand : kChunkCandidates) {
+            build_chunks(b, cand, ch);
+            b->nchunks = (int)ch.size();
+            cudaMemcpy(b->chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice);
+            cudaMemcpy(b->insts, b->hinst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice);
+            cudaStream_t s = b->stream;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 5; ++r) {
+                    if (precision == CH_MIXED)
+                        BLAUNCH_T(kb_tstage, float, b->insts, b->chunks, b->ctrls, (const float *)b->W[0], (const float *)b->D, (float *)b->t);
+                    else
+                        BLAUNCH_T(kb_tstage, double, b->insts, b->chunks, b->ctrls, (const double *)b->F[0], (const double *)b->D, (double *)b->t);
+                }
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (ms < best_ms) { best_ms = ms; best = cand; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        int zero = 0;
+        for (int i = 0; i < count; ++i)
+            cudaMemcpy(&b->ctrls[i].active, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        b->chunk_len = best;
+        build_chunks(b, best, ch);
+        b->nchunks = (int)ch.size();
+        cudaMemcpy(b->chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(b->insts, b->hinst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice);
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cleanup("chunk autotuning", e);
+    }
+    *out = b;
+    return CH_OK;
+}
+
+ch_status ch_batch_layout(const ch_batch *b, int64_t *offsets, int *chunk_len) {
+    if (!b) return bfail(CH_EINVAL, "null batch");
+    if (offsets)
+        for (int i = 0; i <= b->count; ++i) offsets[i] = b->offsets[i];
+    if (chunk_len) *chunk_len = b->chunk_len;
+    return CH_OK;
+}
+
+ch_status ch_integrate_batch(ch_batch *b, const ch_params *prm, double *y, ch_stats *stats) {
+    if (!b || !prm || !y) return bfail(CH_EINVAL, "null argument");
+    if (prm->scheme != CH_EE2 || !prm->adaptive)
+        return bfail(CH_EINVAL, "the batch integrator runs adaptive EE2 (Fig. 4)");
+    if (prm->eyre) return bfail(CH_EINVAL, "the batch integrator has no Eyre splitting");
+    if (!(prm->T > 0.0) || !(prm->tau0 > 0.0) || !(prm->tol > 0.0))
+        return bfail(CH_EINVAL, "T, tau0 and tol must be > 0");
+    if (prm->mmax < 1 || prm->mmax > b->mmax_cap) return bfail(CH_EINVAL, "mmax outside [1, capacity]");
+    if (prm->max_steps < 1) return bfail(CH_EINVAL, "max_steps must be >= 1");
+    return b->precision == CH_MIXED ? integrate_b<float>(b, prm, y, stats)
+                                    : integrate_b<double>(b, prm, y, stats);
+}
+
+int64_t ch_batch_kernel_launches(const ch_batch *b) { return b ? b->launches : 0; }
+
+}  // extern "C"

@@ -19,7 +19,7 @@
 namespace ch {
 
 constexpr int kThreads = 256;          // threads per block of the streaming kernels
-constexpr int kMaxBlocks = 152 * 8;    // 152 SMs x 8 resident blocks of 256 threads
+constexpr int kBlocksPerSM = 4;        // grid of the streaming kernels: 4 x 256 threads per SM
 constexpr int kMaxRed = 4;             // values reduced by one kernel at most
 
 // Periodic grid geometry, passed by value.  -A = discrete Laplacian, h_a = 1/n_a:
@@ -71,19 +71,23 @@ __device__ __forceinline__ void warp_sum(double (&v)[K]) {
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
 }
 
-// Block-wide sum of K values; result valid in thread 0.  Fixed tree => deterministic.
+// Block-wide sum of K values; result valid in thread 0.  Fixed order => deterministic.
+// FP64 adds issue at 2 lanes/clk/SM on GB300, so a shuffle tree in every warp is costly:
+// the per-thread values go to shared memory and one warp adds them (a strided pass, then
+// a 5-level shuffle tree), about a quarter of the FP64 warp instructions of a per-warp tree.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K]) {
-    __shared__ double sh[K][kThreads / 32];
-    warp_sum<K>(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
+    __shared__ double sh[K][kThreads];
 #pragma unroll
-        for (int k = 0; k < K; ++k) sh[k][wid] = v[k];
+    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = v[k];
     __syncthreads();
-    if (wid == 0) {
+    if (threadIdx.x < 32) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) v[k] = (lane < (int)(blockDim.x >> 5)) ? sh[k][lane] : 0.0;
+        for (int k = 0; k < K; ++k) {
+            double a = 0.0;
+            for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) a += sh[k][i];
+            v[k] = a;
+        }
         warp_sum<K>(v);
     }
     __syncthreads();
@@ -114,7 +118,7 @@ __device__ __forceinline__ void grid_sum(double (&v)[K], double *partials, unsig
         for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
             acc[k] += __ldcg(&partials[k * gridDim.x + b]);
     }
-    block_sum<K>(acc);
+    block_sum<K>(acc);          // same code and order in whichever block is last
     if (threadIdx.x == 0) {
         fin(acc);
         *ticket = 0u;
@@ -228,5 +232,8 @@ void launch_krylov_arm(const Launch &L, double tau0, double tol_phi_fixed, doubl
 int phi_setup();
 void launch_phi(const Launch &L, double *H, int ldh, int j, int mmax, double *u,
                 double *scratch);
+// Batched projected phi: one 8-CTA cluster per instance, j + 1 <= 64.
+void launch_phi_batch(const Launch &L, Ctrl *ctrls, double *Hs, int64_t hstride, double *us,
+                      int64_t ustride, int ldh, int j, int mmax, int count);
 
 }  // namespace ch

@@ -7,40 +7,80 @@
 // integer sq >= 0 with ||M||_1 / 2^sq <= theta_13, found by exact halving.  The Pade
 // denominator system is solved by Gauss-Jordan elimination with partial pivoting.
 // All matrices (n = j+1 <= 129) live in shared memory when n <= 64, else in global scratch.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "ch_internal.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace ch {
 
 constexpr int kPhiThreads = 512;
+constexpr int kPhiCluster = 8;     // CTAs of the cluster that shares the matrix products
 constexpr int kPhiSmemMaxN = 64;
 constexpr int kMaxHalvings = 60;   // fixed trace rule of Fig. 2 lines 16-17
 constexpr int kBisections = 12;
+
+constexpr int kTraceSlots = kBisections + 1;   // exp(M(lo0 / 2^b)), b = 0..12
+constexpr int kTraceMaxN = 32;                  // trace by products when n <= 32
 
 struct PhiWork {
     double *b[6];       // six n x n buffers (row-major, ld = n)
     double *fcol;       // n
     double *colsum;     // n
+    double *slot[kTraceSlots];  // trace matrices (nullptr when the trace uses fresh evaluations)
+    double *cur, *tmp;  // trace: exp(M(lo)) and scratch
     double c[14];       // Pade coefficients
+    double chain[64];   // (j-1, j) entry of exp(M(s / 2^m)), m = 0..sq, from the squarings
+    int sq;
     int piv;
     double pinv;
     double norm1;
     double res;
+    double entry;
 };
 
-__device__ __forceinline__ void mm(int n, const double *A, const double *B, double *C) {
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int r = e / n, c = e - r * n;
-        double acc = 0.0;
-        for (int k = 0; k < n; ++k) acc = fma(A[r * n + k], B[k * n + c], acc);
-        C[e] = acc;
+// C = A B on one thread block.
+struct MatmulBlock {
+    __device__ __forceinline__ void operator()(int n, const double *A, const double *B,
+                                               double *C) const {
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int r = e / n, c = e - r * n;
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc = fma(A[r * n + k], B[k * n + c], acc);
+            C[e] = acc;
+        }
+        __syncthreads();
     }
-    __syncthreads();
-}
+};
+
+// C = A B on a cluster: every CTA holds the same copies of A and B in its shared memory,
+// computes a slice of rows of C and stores it into the C of every CTA of the cluster
+// (distributed shared memory).  Cluster barriers before (nobody still reads C) and after
+// (all slices arrived).
+struct MatmulCluster {
+    __device__ __forceinline__ void operator()(int n, const double *A, const double *B,
+                                               double *C) const {
+        cg::cluster_group cl = cg::this_cluster();
+        const int rank = (int)cl.block_rank(), nr = (int)cl.num_blocks();
+        const int r0 = rank * n / nr, r1 = (rank + 1) * n / nr;
+        double *dst[kPhiCluster];
+        for (int q = 0; q < nr; ++q) dst[q] = cl.map_shared_rank(C, q);
+        cl.sync();
+        for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
+            const int r = r0 + e / n, c = e - (r - r0) * n;
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc = fma(A[r * n + k], B[k * n + c], acc);
+            for (int q = 0; q < nr; ++q) dst[q][r * n + c] = acc;
+        }
+        cl.sync();
+    }
+};
 
 // E = exp(M) with M given in W.b[0]; returns the buffer holding E.
-__device__ double *expm_block(int n, PhiWork &W) {
+template <typename MM>
+__device__ double *expm_block(int n, PhiWork &W, const MM &mm) {
     double *X = W.b[0], *X2 = W.b[1], *X4 = W.b[2], *X6 = W.b[3], *T4 = W.b[4], *T5 = W.b[5];
     const int nn = n * n;
     // ||M||_1 (max column sum)
@@ -134,16 +174,26 @@ __device__ double *expm_block(int n, PhiWork &W) {
         __syncthreads();
     }
     double *R = Q, *S = X6;
+    // R = exp(M / 2^sq); record its (n-2, n-1) entry (the residual entry of Fig. 2 line 12)
+    // for s / 2^sq, then after each squaring for s / 2^(sq-k-1)
+    if (threadIdx.x == 0) {
+        W.sq = sq;
+        if (sq < 64) W.chain[sq] = R[(n - 2) * n + (n - 1)];
+    }
     for (int k = 0; k < sq; ++k) {
         mm(n, R, R, S);
         double *t = R; R = S; S = t;
+        if (threadIdx.x == 0 && sq - k - 1 < 64) W.chain[sq - k - 1] = R[(n - 2) * n + (n - 1)];
     }
+    __syncthreads();
     return R;
 }
 
-// u = s phi(-s H_j) e_1 into W.fcol[0..j-1]... (u written to `u`), returns resnorm.
+// u = s phi(-s H_j) e_1 (written to `u` when u != nullptr, else kept in W.fcol); returns
+// resnorm = h_{j+1,j} |e_j^T u| (Fig. 2 line 12).
+template <typename MM>
 __device__ double phi_eval(int j, const double *H, int ldh, double hnext, double s, double *u,
-                           PhiWork &W) {
+                           PhiWork &W, const MM &mm) {
     const int n = j + 1;
     double *M = W.b[0];
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -154,24 +204,30 @@ __device__ double phi_eval(int j, const double *H, int ldh, double hnext, double
         M[e] = v;
     }
     __syncthreads();
-    const double *E = expm_block(n, W);
-    for (int r = threadIdx.x; r < j; r += blockDim.x) u[r] = E[r * n + j];
+    const double *E = expm_block(n, W, mm);
+    const double last = E[(j - 1) * n + j];
+    if (u)
+        for (int r = threadIdx.x; r < j; r += blockDim.x) u[r] = E[r * n + j];
     __syncthreads();
-    return hnext * fabs(u[j - 1]);                      // Fig. 2 line 12
+    return hnext * fabs(last);                          // Fig. 2 line 12
 }
 
-__global__ void __launch_bounds__(kPhiThreads)
-k_phi(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double *u, double *gscratch,
-      int use_smem) {
-    if (!ctrl->active) return;
-    extern __shared__ double smem[];
+// Fig. 2 lines 9-20 for iteration j, on one CTA (MM = MatmulBlock) or one cluster (every
+// CTA runs the same control flow on identical data; rank 0 alone writes results).
+template <typename MM>
+__device__ void phi_step(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double *u,
+                         double *base, bool writer, const MM &mm, bool base_has_slots) {
     __shared__ PhiWork W;
     const int n = j + 1;
     if (threadIdx.x == 0) {
-        double *base = use_smem ? smem : gscratch;
         for (int k = 0; k < 6; ++k) W.b[k] = base + (size_t)k * n * n;
         W.fcol = base + (size_t)6 * n * n;
         W.colsum = W.fcol + n;
+        const bool trace_slots = (j == mmax) && n <= kTraceMaxN && base_has_slots;
+        double *sb = W.colsum + n;
+        for (int k = 0; k < kTraceSlots; ++k) W.slot[k] = trace_slots ? sb + (size_t)k * n * n : nullptr;
+        W.cur = trace_slots ? sb + (size_t)kTraceSlots * n * n : nullptr;
+        W.tmp = trace_slots ? W.cur + (size_t)n * n : nullptr;
         W.c[0] = 1.0;
         for (int k = 1; k <= 13; ++k)
             W.c[k] = W.c[k - 1] * (double)(13 - k + 1) / ((double)(2 * 13 - k + 1) * k);
@@ -179,10 +235,9 @@ k_phi(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double *u, double *gscrat
     __syncthreads();
     const double hnext = sqrt(ctrl->hnext2);             // Fig. 2 line 9
     const double tau0 = ctrl->tau0, tol = ctrl->tol_phi;
-    if (threadIdx.x == 0) H[j * ldh + (j - 1)] = hnext;
-    __syncthreads();
+    double *uo = writer ? u : nullptr;
     int evals = 1;
-    double res = phi_eval(j, H, ldh, hnext, tau0, u, W);  // lines 10-12
+    double res = phi_eval(j, H, ldh, hnext, tau0, uo, W, mm);  // lines 10-12
     int done = 0, shrunk = 0, status = 0;
     double tau = tau0;
     if (!isfinite(hnext) || !isfinite(res)) {
@@ -191,31 +246,74 @@ k_phi(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double *u, double *gscrat
     } else if (res <= tol) {                                // lines 13-14
         done = 1;
     } else if (j == mmax) {                                 // lines 15-19
-        double lo = tau0, hi = tau0;
-        int ok = 0;
-        for (int k = 0; k < kMaxHalvings; ++k) {
-            hi = lo;
-            lo = 0.5 * lo;
-            ++evals;
-            if (phi_eval(j, H, ldh, hnext, lo, u, W) <= tol) { ok = 1; break; }
-        }
-        if (ok) {
-            for (int k = 0; k < kBisections; ++k) {
-                const double mid = 0.5 * (lo + hi);
+        // Halve s from tau0 until resnorm(s) <= tol_phi: the trials s = tau0/2^k with
+        // k <= sq are the intermediate squarings of the evaluation at tau0 (same arithmetic
+        // as a fresh evaluation, whose scaling exponent is sq - k), recorded in W.chain.
+        const int sq0 = W.sq;
+        int k = 0, ok = 0;
+        for (k = 1; k <= kMaxHalvings; ++k) {
+            double r;
+            if (k <= sq0 && k < 64) {
+                r = hnext * fabs(W.chain[k]);
+            } else {
                 ++evals;
-                if (phi_eval(j, H, ldh, hnext, mid, u, W) <= tol) lo = mid;
-                else hi = mid;
+                r = phi_eval(j, H, ldh, hnext, ldexp(tau0, -k), nullptr, W, mm);
             }
+            if (r <= tol) { ok = 1; break; }
+        }
+        if (!ok) {
+            status = CH_ENOTCONV;
+        } else if (W.slot[0] != nullptr) {
+            // Bisection between lo0 = tau0/2^k (admissible) and 2 lo0: the trials are
+            // lo + lo0/2^b, and M(s) is linear in s, so exp(M(lo + d)) = exp(M(lo)) exp(M(d)).
+            // slot[b] = exp(M(lo0/2^b)) comes from one evaluation at lo0/2^12 and squarings.
+            const double lo0 = ldexp(tau0, -k);
             ++evals;
-            phi_eval(j, H, ldh, hnext, lo, u, W);           // line 18
+            phi_eval(j, H, ldh, hnext, ldexp(lo0, -kBisections), nullptr, W, mm);
+            const double *E = (W.sq % 2 == 0) ? W.b[2] : W.b[3];
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) W.slot[kBisections][e] = E[e];
+            __syncthreads();
+            for (int b = kBisections - 1; b >= 0; --b) mm(n, W.slot[b + 1], W.slot[b + 1], W.slot[b]);
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) W.cur[e] = W.slot[0][e];
+            __syncthreads();
+            double lo = lo0;
+            for (int b = 1; b <= kBisections; ++b) {
+                if (threadIdx.x == 0) {          // (j-1, j) entry of exp(M(lo)) exp(M(lo0/2^b))
+                    double acc = 0.0;
+                    for (int c = 0; c < n; ++c) acc = fma(W.cur[(j - 1) * n + c], W.slot[b][c * n + j], acc);
+                    W.entry = acc;
+                }
+                __syncthreads();
+                if (hnext * fabs(W.entry) <= tol) {
+                    mm(n, W.cur, W.slot[b], W.tmp);
+                    if (threadIdx.x == 0) { double *t = W.cur; W.cur = W.tmp; W.tmp = t; }
+                    __syncthreads();
+                    lo += ldexp(lo0, -b);
+                }
+            }
+            if (uo)                                      // line 18: u = s phi(-s H) e_1 at s = lo
+                for (int r = threadIdx.x; r < j; r += blockDim.x) uo[r] = W.cur[r * n + j];
+            __syncthreads();
             tau = lo;
             shrunk = 1;
         } else {
-            status = CH_ENOTCONV;
+            double lo = ldexp(tau0, -k), hi = 2.0 * lo;
+            for (int b = 0; b < kBisections; ++b) {
+                const double mid = 0.5 * (lo + hi);
+                ++evals;
+                if (phi_eval(j, H, ldh, hnext, mid, uo, W, mm) <= tol) lo = mid;
+                else hi = mid;
+            }
+            ++evals;
+            phi_eval(j, H, ldh, hnext, lo, uo, W, mm);      // line 18
+            tau = lo;
+            shrunk = 1;
         }
         done = 1;
     }
+    if (!writer) return;
     if (threadIdx.x == 0) {
+        H[j * ldh + (j - 1)] = hnext;
         ctrl->phi_evals += evals;
         ctrl->resnorm = res;
         if (done) {
@@ -238,18 +336,102 @@ k_phi(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double *u, double *gscrat
             ctrl->coef[c] = ctrl->beta * ctrl->gam[c] * u[c];   // line 23
 }
 
-int phi_setup() {
-    const size_t bytes = (size_t)(6 * kPhiSmemMaxN * kPhiSmemMaxN + 2 * kPhiSmemMaxN) * sizeof(double);
-    return (int)cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+__global__ void __launch_bounds__(kPhiThreads)
+k_phi(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double *u, double *gscratch,
+      int use_smem) {
+    if (!ctrl->active) return;
+    extern __shared__ double smem[];
+    phi_step(ctrl, H, ldh, j, mmax, u, use_smem ? smem : gscratch, true, MatmulBlock(),
+             use_smem != 0);
 }
 
+__global__ void __launch_bounds__(kPhiThreads)
+k_phi_cluster(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double *u) {
+    if (!ctrl->active) return;                 // same value in every CTA of the cluster
+    extern __shared__ double smem[];
+    const bool writer = cg::this_cluster().block_rank() == 0;
+    phi_step(ctrl, H, ldh, j, mmax, u, smem, writer, MatmulCluster(), true);
+}
+
+// Batched form: one cluster per instance (cluster index = instance), each with its own
+// control block, Hessenberg matrix (stride hstride) and u (stride ustride).
+__global__ void __launch_bounds__(kPhiThreads)
+k_phi_batch(Ctrl *ctrls, double *Hs, int64_t hstride, double *us, int64_t ustride, int ldh,
+            int j, int mmax) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int inst = (int)(blockIdx.x / cl.num_blocks());
+    Ctrl *ctrl = ctrls + inst;
+    if (!ctrl->active) return;                 // same value in every CTA of this cluster
+    extern __shared__ double smem[];
+    const bool writer = cl.block_rank() == 0;
+    phi_step(ctrl, Hs + inst * hstride, ldh, j, mmax, us + inst * ustride, smem, writer,
+             MatmulCluster(), true);
+}
+
+// Dynamic shared memory of one phi launch: six work matrices and two vectors, plus the
+// trace matrices when j == mmax and n <= 32.
+static size_t phi_smem_bytes(int n, int j, int mmax) {
+    size_t words = (size_t)6 * n * n + 2 * n;
+    if (j == mmax && n <= kTraceMaxN) words += (size_t)(kTraceSlots + 2) * n * n;
+    return words * sizeof(double);
+}
+
+int phi_setup() {
+    const size_t bytes = (size_t)(6 * kPhiSmemMaxN * kPhiSmemMaxN + 2 * kPhiSmemMaxN) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_phi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_phi_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return (int)e;
+}
+
+// Small systems (n <= 8) stay on one CTA; up to 64 they use an 8-CTA cluster with the
+// matrices in shared memory; beyond 64 one CTA works from global scratch.
 void launch_phi(const Launch &L, double *H, int ldh, int j, int mmax, double *u,
                 double *scratch) {
     const int n = j + 1;
-    const int use_smem = n <= kPhiSmemMaxN;
-    const size_t bytes = use_smem ? (size_t)(6 * n * n + 2 * n) * sizeof(double) : 0;
     LaunchScope scope(L, CH_K_PHI);
+    if (n > 8 && n <= kPhiSmemMaxN) {
+        const size_t bytes = phi_smem_bytes(n, j, mmax);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kPhiCluster, 1, 1);
+        cfg.blockDim = dim3(kPhiThreads, 1, 1);
+        cfg.dynamicSmemBytes = bytes;
+        cfg.stream = L.stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kPhiCluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_phi_cluster, L.ctrl, H, ldh, j, mmax, u);
+        return;
+    }
+    const int use_smem = n <= kPhiSmemMaxN;
+    const size_t bytes = use_smem ? phi_smem_bytes(n, j, mmax) : 0;
     k_phi<<<1, kPhiThreads, bytes, L.stream>>>(L.ctrl, H, ldh, j, mmax, u, scratch, use_smem);
+}
+
+void launch_phi_batch(const Launch &L, Ctrl *ctrls, double *Hs, int64_t hstride, double *us,
+                      int64_t ustride, int ldh, int j, int mmax, int count) {
+    const int n = j + 1;
+    LaunchScope scope(L, CH_K_PHI);
+    const size_t bytes = phi_smem_bytes(n, j, mmax);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kPhiCluster * count, 1, 1);
+    cfg.blockDim = dim3(kPhiThreads, 1, 1);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kPhiCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_phi_batch, ctrls, Hs, hstride, us, ustride, ldh, j, mmax);
 }
 
 }  // namespace ch

@@ -68,6 +68,19 @@ template <> struct DotAcc<float> {
 #define GRID_LOOP(i, N) \
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < (unsigned)(N); i += gridDim.x * blockDim.x)
 
+// Grid-stride loop that handles two elements (i, i + stride) per trip, so each thread has
+// twice the loads in flight; per-thread accumulation order is the same as GRID_LOOP's.
+#define GRID_LOOP2(N, ...)                                                                \
+    {                                                                                     \
+        const unsigned stride_ = gridDim.x * blockDim.x;                                  \
+        unsigned i_ = blockIdx.x * blockDim.x + threadIdx.x;                              \
+        for (; i_ + stride_ < (unsigned)(N); i_ += 2 * stride_) {                         \
+            { const unsigned i = i_; __VA_ARGS__ }                                        \
+            { const unsigned i = i_ + stride_; __VA_ARGS__ }                              \
+        }                                                                                 \
+        if (i_ < (unsigned)(N)) { const unsigned i = i_; __VA_ARGS__ }                    \
+    }
+
 // ---------------------------------------------------------------------------------------
 // Per-step preparation from the linearisation point y^n:
 //   D = 3 y^2 - 1 (+1 Eyre) + eps^2 sigma   (diagonal of J_n + eps^2 A [+I] before -kap sums)
@@ -124,7 +137,7 @@ k_tstage(Geom g, const VT *__restrict__ x, const VT *__restrict__ D, VT *__restr
          const Ctrl *ctrl, int guarded) {
     if (guarded && !ctrl->active) return;
     const VT k0 = (VT)g.kap[0], k1 = (VT)g.kap[1], k2 = (VT)g.kap[2];
-    GRID_LOOP(i, g.N) {
+    GRID_LOOP2(g.N, {
         VT ps[3];
         pair_sums<DIM>(g, x, i, ps);
         VT acc = D[i] * x[i];
@@ -132,7 +145,7 @@ k_tstage(Geom g, const VT *__restrict__ x, const VT *__restrict__ D, VT *__restr
         acc = fma(-k1, ps[1], acc);
         if (DIM == 3) acc = fma(-k2, ps[2], acc);
         t[i] = acc;
-    }
+    })
 }
 
 template <int DIM, typename VT>
@@ -144,7 +157,7 @@ k_wstage(Geom g, const VT *__restrict__ t, VT *__restrict__ w, const VT *__restr
     const VT c0 = (VT)(gam * g.sigma), c1 = (VT)(gam * g.s[0]), c2 = (VT)(gam * g.s[1]),
              c3 = (VT)(gam * g.s[2]);
     DotAcc<VT> acc;
-    GRID_LOOP(i, g.N) {
+    GRID_LOOP2(g.N, {
         VT ps[3];
         pair_sums<DIM>(g, t, i, ps);
         VT r = c0 * t[i];
@@ -153,7 +166,7 @@ k_wstage(Geom g, const VT *__restrict__ t, VT *__restrict__ w, const VT *__restr
         if (DIM == 3) r = fma(-c3, ps[2], r);
         w[i] = r;
         if (v1) acc.add(r, v1[i]);
-    }
+    })
     if (!v1) return;
     double tot1[1] = {acc.value()};
     grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { *hout = ctrl->gam[0] * tot[0]; });
@@ -164,31 +177,53 @@ k_wstage(Geom g, const VT *__restrict__ t, VT *__restrict__ w, const VT *__restr
 //   w -= h_{kj} v_k  (= h_{kj} gam_k W_k),  then  h_{k+1,j} = w . v_{k+1}   (k < j)
 //                                           or    ||w||^2 for line 9       (k = j)
 // ---------------------------------------------------------------------------------------
+// 16-byte vectors of the basis precision: double2 / float4.
+template <typename VT> struct Vec16;
+template <> struct Vec16<double> { typedef double2 T; static constexpr int W = 2; };
+template <> struct Vec16<float> { typedef float4 T; static constexpr int W = 4; };
+
+template <typename V> __device__ __forceinline__ auto &lane(V &v, int k);
+__device__ __forceinline__ double &lane(double2 &v, int k) { return k == 0 ? v.x : v.y; }
+__device__ __forceinline__ float &lane(float4 &v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
 template <typename VT>
 __global__ void __launch_bounds__(kThreads)
 k_mgs(int64_t N, VT *__restrict__ w, const VT *__restrict__ vk, const VT *__restrict__ vk1,
       const double *hk, double *hout, int k, int last, double *partials, unsigned int *ticket,
       Ctrl *ctrl) {
     if (!ctrl->active) return;
+    typedef typename Vec16<VT>::T V;
+    constexpr int WD = Vec16<VT>::W;
     const VT c = (VT)(*hk * ctrl->gam[k - 1]);
     DotAcc<VT> acc;
-    if (!last) {
-        GRID_LOOP(i, N) {
-            const VT r = fma(-c, vk[i], w[i]);
-            w[i] = r;
-            acc.add(r, vk1[i]);
+    // all vectors start on 256-byte boundaries; the N % WD tail is done element by element
+    const unsigned nv = (unsigned)(N / WD);
+    V *w4 = reinterpret_cast<V *>(w);
+    const V *a4 = reinterpret_cast<const V *>(vk);
+    const V *b4 = reinterpret_cast<const V *>(last ? vk : vk1);
+    GRID_LOOP2(nv, {
+        V x = w4[i];
+        const V a = a4[i], b = b4[i];
+        for (int q = 0; q < WD; ++q) {      // WD is a compile-time constant: fully unrolled
+            const VT r = fma(-c, lane(const_cast<V &>(a), q), lane(x, q));
+            lane(x, q) = r;
+            acc.add(r, last ? r : lane(const_cast<V &>(b), q));
         }
-        double tot1[1] = {acc.value()};
-        grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { *hout = ctrl->gam[k] * tot[0]; });
-    } else {
-        GRID_LOOP(i, N) {
-            const VT r = fma(-c, vk[i], w[i]);
-            w[i] = r;
-            acc.add(r, r);
-        }
-        double tot1[1] = {acc.value()};
-        grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { ctrl->hnext2 = tot[0]; });
+        w4[i] = x;
+    })
+    for (int64_t i = (int64_t)nv * WD + blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const VT r = fma(-c, vk[i], w[i]);
+        w[i] = r;
+        acc.add(r, last ? r : vk1[i]);
     }
+    double tot1[1] = {acc.value()};
+    if (!last)
+        grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { *hout = ctrl->gam[k] * tot[0]; });
+    else
+        grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { ctrl->hnext2 = tot[0]; });
 }
 
 // ---------------------------------------------------------------------------------------
@@ -203,12 +238,12 @@ k_combine(int64_t N, const double *__restrict__ y0, const double *__restrict__ v
     __shared__ double coef[130];
     for (int c = threadIdx.x; c < j; c += blockDim.x) coef[c] = ctrl->coef[c];
     __syncthreads();
-    GRID_LOOP(i, N) {
+    GRID_LOOP2(N, {
         double acc = 0.0;
         if (j > 0) acc = coef[0] * v0[i];
         for (int c = 1; c < j; ++c) acc = fma(coef[c], V[(c - 1) * ldv + i], acc);
         ynext[i] = y0[i] + acc;
-    }
+    })
 }
 
 // Mixed precision, pass 1: increment d = sum_c coef_c W_c in FP32 and its sum (mass) in
@@ -263,7 +298,7 @@ __global__ void __launch_bounds__(kThreads)
 k_rhs1(Geom g, const double *__restrict__ y, int eyre, double *__restrict__ mu,
        double *__restrict__ q) {
     const double cshift = g.eps2 * g.sigma - 1.0;
-    GRID_LOOP(i, g.N) {
+    GRID_LOOP2(g.N, {
         double ps[3];
         pair_sums<DIM>(g, y, i, ps);
         const double yi = y[i];
@@ -274,10 +309,10 @@ k_rhs1(Geom g, const double *__restrict__ y, int eyre, double *__restrict__ mu,
         if (DIM == 3) m = fma(-g.kap[2], ps[2], m);
         mu[i] = m;
         if (q) q[i] = eyre ? fma(2.0 * y2, yi, yi) : 2.0 * y2 * yi;
-    }
+    })
 }
 
-template <int DIM>
+template <int DIM, int K>
 __global__ void __launch_bounds__(kThreads)
 k_rhs2(Geom g, const double *__restrict__ mu, const double *__restrict__ q,
        double *__restrict__ f, const double *__restrict__ y0, const double *__restrict__ f0,
@@ -285,7 +320,7 @@ k_rhs2(Geom g, const double *__restrict__ mu, const double *__restrict__ q,
        unsigned int *ticket, Ctrl *ctrl) {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     if (mode & 8) half_tau = 0.5 * ctrl->tau;
-    GRID_LOOP(i, g.N) {
+    GRID_LOOP2(g.N, {
         double ps[3];
         pair_sums<DIM>(g, mu, i, ps);
         double r = -g.sigma * mu[i];
@@ -309,11 +344,15 @@ k_rhs2(Geom g, const double *__restrict__ mu, const double *__restrict__ q,
             acc[2] = fma(d, d, acc[2]);
             acc[3] = fma(ypc, ypc, acc[3]);
         }
+    })
+    if constexpr (K > 0) {
+        double red[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k] = acc[k];
+        grid_sum<K>(red, partials, ticket, [&](double (&tot)[K]) {
+            for (int k = 0; k < 4; ++k) ctrl->red[k] = k < K ? tot[k] : 0.0;
+        });
     }
-    if (!(mode & 7)) return;
-    grid_sum<4>(acc, partials, ticket, [&](double (&tot)[4]) {
-        for (int k = 0; k < 4; ++k) ctrl->red[k] = tot[k];
-    });
 }
 
 // ---------------------------------------------------------------------------------------
@@ -327,7 +366,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_resid1(Geom g, const double *__restrict__ x, const double *__restrict__ D,
          const double *__restrict__ G, double *__restrict__ t) {
-    GRID_LOOP(i, g.N) {
+    GRID_LOOP2(g.N, {
         double ps[3];
         pair_sums<DIM>(g, x, i, ps);
         double acc = fma(-D[i], x[i], G[i]);
@@ -335,7 +374,7 @@ k_resid1(Geom g, const double *__restrict__ x, const double *__restrict__ D,
         acc = fma(g.kap[1], ps[1], acc);
         if (DIM == 3) acc = fma(g.kap[2], ps[2], acc);
         t[i] = acc;
-    }
+    })
 }
 
 template <int DIM>
@@ -343,7 +382,7 @@ __global__ void __launch_bounds__(kThreads)
 k_resid2(Geom g, const double *__restrict__ t, double *__restrict__ out, double *partials,
          unsigned int *ticket, Ctrl *ctrl) {
     double acc[1] = {0.0};
-    GRID_LOOP(i, g.N) {
+    GRID_LOOP2(g.N, {
         double ps[3];
         pair_sums<DIM>(g, t, i, ps);
         double r = g.sigma * t[i];
@@ -352,7 +391,7 @@ k_resid2(Geom g, const double *__restrict__ t, double *__restrict__ out, double 
         if (DIM == 3) r = fma(-g.s[2], ps[2], r);
         out[i] = r;
         acc[0] = fma(r, r, acc[0]);
-    }
+    })
     grid_sum<1>(acc, partials, ticket, [&](double (&tot)[1]) { ctrl->red[0] = tot[0]; });
 }
 
@@ -366,7 +405,7 @@ k_lim2(Geom g, const double *__restrict__ t, const double *__restrict__ yn,
     const double at = alpha * tau;
     const double c0 = at * g.sigma, c1 = at * g.s[0], c2 = at * g.s[1], c3 = at * g.s[2];
     const double ca = alpha * tau_a;
-    GRID_LOOP(i, g.N) {
+    GRID_LOOP2(g.N, {
         double ps[3];
         pair_sums<DIM>(g, t, i, ps);
         double r = c0 * t[i];
@@ -374,7 +413,7 @@ k_lim2(Geom g, const double *__restrict__ t, const double *__restrict__ yn,
         r = fma(-c2, ps[1], r);
         if (DIM == 3) r = fma(-c3, ps[2], r);
         ynext[i] = fma(ca, yprev[i], fma(alpha, yn[i], r));
-    }
+    })
 }
 
 // Energy of Eq. (Ediscr) (periodic forward differences) and mass: red[6], red[7] (unscaled
@@ -525,8 +564,22 @@ void launch_rhs1(const Launch &L, const Geom &g, const double *y, int eyre, doub
 void launch_rhs2(const Launch &L, const Geom &g, const double *mu, const double *q,
                  double *f, const double *y0, const double *f0, const double *y1,
                  double half_tau, int mode) {
-    DISPATCH_DIM(CH_K_RHS2, g, k_rhs2, g, mu, q, f, y0, f0, y1, half_tau, mode, L.partials,
-                 &L.ctrl->ticket[0], L.ctrl);
+    // number of reduced values: the highest of ||f||^2, ||g_hat||^2, est sums requested
+    const int K = (mode & 4) ? 4 : (mode & 2) ? 2 : (mode & 1) ? 1 : 0;
+    LaunchScope scope_(L, CH_K_RHS2);
+#define RHS2_ARGS g, mu, q, f, y0, f0, y1, half_tau, mode, L.partials, &L.ctrl->ticket[0], L.ctrl
+    if (g.dim == 3) {
+        if (K == 4) k_rhs2<3, 4><<<L.blocks, kThreads, 0, L.stream>>>(RHS2_ARGS);
+        else if (K == 2) k_rhs2<3, 2><<<L.blocks, kThreads, 0, L.stream>>>(RHS2_ARGS);
+        else if (K == 1) k_rhs2<3, 1><<<L.blocks, kThreads, 0, L.stream>>>(RHS2_ARGS);
+        else k_rhs2<3, 0><<<L.blocks, kThreads, 0, L.stream>>>(RHS2_ARGS);
+    } else {
+        if (K == 4) k_rhs2<2, 4><<<L.blocks, kThreads, 0, L.stream>>>(RHS2_ARGS);
+        else if (K == 2) k_rhs2<2, 2><<<L.blocks, kThreads, 0, L.stream>>>(RHS2_ARGS);
+        else if (K == 1) k_rhs2<2, 1><<<L.blocks, kThreads, 0, L.stream>>>(RHS2_ARGS);
+        else k_rhs2<2, 0><<<L.blocks, kThreads, 0, L.stream>>>(RHS2_ARGS);
+    }
+#undef RHS2_ARGS
 }
 
 void launch_resid1(const Launch &L, const Geom &g, const double *x, const double *D,

@@ -1,0 +1,83 @@
+"""Batched adaptive EE2 (many independent instances of uneven size and eps in one launch
+sequence) against the oracle run of every instance on its own."""
+import numpy as np
+import pytest
+
+from paper_2502_14589_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ch():
+    from paper_2502_14589_gb300 import build, ch as chmod
+    build.build()
+    chmod.load()
+    return chmod
+
+
+def run_batch(ch, dim, sizes, eps, y0s, precision, T, tol=1e-5, tau0=1e-7, mmax=30):
+    h = ch.ch_create_batch(dim, sizes, eps, precision, mmax)
+    try:
+        offs, chunk = ch.ch_batch_layout(h, len(sizes))
+        y = torch.zeros(offs[-1], dtype=torch.float64, device="cuda")
+        for i, y0 in enumerate(y0s):
+            y[offs[i]:offs[i] + y0.size] = torch.from_numpy(y0).cuda()
+        st = ch.ch_integrate_batch(h, ch.make_params("ee2", True, T, tau0, tol, mmax), y, len(sizes))
+        torch.cuda.synchronize()
+        yh = y.cpu().numpy()
+        return [yh[offs[i]:offs[i] + y0s[i].size] for i in range(len(sizes))], st, chunk
+    finally:
+        ch.ch_destroy_batch(h)
+
+
+def oracle_run(oracle, dim, n, eps, y0, T, tol=1e-5, tau0=1e-7, mmax=30):
+    rc, y, t, st, rec = oracle.integrate(oracle.Grid(dim, n, eps), y0, "ee2", True, T, tau0,
+                                         tol=tol, mmax=mmax)
+    assert rc == 0
+    return y, st
+
+
+def test_fp64_batch_matches_oracle_per_instance(ch, oracle):
+    sides = [24, 32, 40, 48, 36, 20]
+    eps = [0.02, 0.05, 0.03, 0.04, 0.025, 0.045]
+    y0s = [inputs.initial_state((s, s), 10 + i) for i, s in enumerate(sides)]
+    T = 3e-5
+    ys, st, chunk = run_batch(ch, 2, sides, eps, y0s, ch.CH_FP64, T)
+    for i, s in enumerate(sides):
+        yo, sto = oracle_run(oracle, 2, (s, s), eps[i], y0s[i], T)
+        err = np.linalg.norm(ys[i] - yo) / np.linalg.norm(yo)
+        assert st[i]["t"] == T
+        assert st[i]["steps"] == sto["steps"], (i, st[i], sto)
+        assert st[i]["matvecs"] == sto["matvecs"], (i, st[i], sto)
+        assert err < 1e-10, (i, err)
+
+
+def test_mixed_batch_error_at_T(ch, oracle):
+    sides = [32, 64, 48, 96]
+    eps = [0.02, 0.04, 0.03, 0.01]
+    y0s = [inputs.initial_state((s, s), 20 + i) for i, s in enumerate(sides)]
+    T = 3e-5
+    ys, st, chunk = run_batch(ch, 2, sides, eps, y0s, ch.CH_MIXED, T, tol=1e-6)
+    for i, s in enumerate(sides):
+        yo, sto = oracle_run(oracle, 2, (s, s), eps[i], y0s[i], T, tol=1e-6)
+        err = np.linalg.norm(ys[i] - yo) / np.linalg.norm(yo)
+        print(f"mixed batch instance {i} side {s}: steps {st[i]['steps']} vs {sto['steps']}, error at T {err:.2e}")
+        assert st[i]["t"] == T
+        assert err < 1e-5
+        assert abs(ys[i].mean() - y0s[i].mean()) < 1e-13
+
+
+def test_batch_3d_and_stationary_instance(ch, oracle):
+    sides = [12, 16, 10]
+    eps = [0.05, 0.04, 0.06]
+    y0s = [inputs.initial_state((s, s, s), 30 + i) for i, s in enumerate(sides)]
+    y0s[1] = np.full(16 ** 3, 0.25)                   # beta = 0: must stay put
+    T = 2e-5
+    ys, st, chunk = run_batch(ch, 3, sides, eps, y0s, ch.CH_FP64, T)
+    assert np.array_equal(ys[1], y0s[1])
+    for i in (0, 2):
+        yo, sto = oracle_run(oracle, 3, (sides[i],) * 3, eps[i], y0s[i], T)
+        assert st[i]["steps"] == sto["steps"]
+        assert np.linalg.norm(ys[i] - yo) / np.linalg.norm(yo) < 1e-10

@@ -186,9 +186,11 @@ def test_adaptive_step_sequence(ch, oracle, scheme, dim, n, eps, T):
     np.testing.assert_array_equal(rec["jexit"], reco["jexit"])
     np.testing.assert_array_equal(rec["shrunk"], reco["shrunk"])
     np.testing.assert_array_equal(rec["p"], reco["p"])
-    # the last step is T - t: it inherits the absolute rounding of the accumulated time t
+    # Every tau carries the rounding of est (a difference of nearly equal vectors, relative
+    # error ~ u/est ~ 1e-11 at tol 1e-5), and LIM's tau_new = (tol/est) tau compounds it over
+    # the run; the last step T - t inherits the accumulated absolute difference of t.
     np.testing.assert_allclose(rec["tau"][:-1], reco["tau"][:-1], rtol=1e-9)
-    assert abs(rec["tau"][-1] - reco["tau"][-1]) <= 1e-10 * T
+    assert abs(rec["tau"][-1] - reco["tau"][-1]) <= 1e-8 * T
     assert abs(st["t"] - T) <= 1e-15 * T
     assert rel(yg, yo) < 1e-10
 
