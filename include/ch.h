@@ -207,6 +207,25 @@ ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us
                           double *bytes_per_launch, double *flops_per_launch,
                           double *fp64_instr_per_launch);
 
+/* ---- Energy and mass without any allocation ------------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot let a library
+ * allocate device memory: applications that hand out all device memory from their own pool
+ * (a caching allocator or a fixed arena sized at start-up), and callers keeping work running
+ * concurrently on several streams, where the device synchronisation that cudaMalloc / cudaFree
+ * may cause would stall it.  It computes what ch_energy_mass computes (discrete energy and
+ * mass of y on a periodic grid of dim 2 or 3 with n[a] >= 1 points per axis, at most
+ * 2^31 - 1 points in all) without a grid object: the caller passes y (device, N doubles) and
+ * out (device, 2 doubles: energy, mass), and the work is queued on cuda_stream without a
+ * synchronisation.  Its reduction scratch is a fixed 16 KiB + 256 B array in the library's
+ * device image (every GPU that loads the library holds it until the process exits); all
+ * calls on a device share it, so calls whose work overlaps on the GPU (different streams, or
+ * unordered host threads) race and must be serialised by the caller.  The first call on each
+ * device does a one-time set-up (it looks up the array's device address with
+ * cudaGetSymbolAddress); make that first call before any stream capture.  Grids beyond
+ * 2^31 - 1 points are rejected with CH_EINVAL.                                               */
+ch_status ch_energy_mass_noalloc(int dim, const int64_t n[3], double eps, const double *y,
+                                 double *out, void *cuda_stream);
+
 /* Message of the last error on the calling thread ("" when none). */
 const char *ch_last_error(void);
 

@@ -70,6 +70,7 @@ _SIGS = {
     "ch_destroy_batch": [_P],
     "ch_batch_layout": [_P, C.POINTER(C.c_int64), _IP],
     "ch_integrate_batch": [_P, C.POINTER(ch_params), _P, C.POINTER(ch_stats)],
+    "ch_energy_mass_noalloc": [C.c_int, C.POINTER(C.c_int64), _D, _P, _P, _P],
 }
 
 KERNEL_CLASSES = ["prep", "tstage", "wstage", "mgs", "phi", "combine", "rhs1", "rhs2",
@@ -312,3 +313,10 @@ def ch_integrate_batch(h, prm, y, count):
 
 def ch_batch_kernel_launches(h):
     return load().ch_batch_kernel_launches(h)
+
+
+def ch_energy_mass_noalloc(dim, n, eps, y, out, stream=None):
+    """Energy and mass of y into the device tensor out[0:2] without any allocation (queued on
+    the stream, not synchronised); see include/ch.h for whom this entry point is for."""
+    nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    _check(load().ch_energy_mass_noalloc(dim, nn, eps, _ptr(y), _ptr(out), _stream(stream)))
