@@ -380,64 +380,10 @@ def main():
     # (CUDA events on the grid's stream around a graph of back-to-back launches); the
     # dominant class is the one with the largest launches x mean duration in the timed region
     kernels = {}
-    for cls in (() if args.no_roofline else ("tstage", "wstage", "mgs", "resid1", "lim2", "rhs1", "rhs2")):
-        kb = ch.ch_bench_kernel(G.h, cls, 200)
-        dur = kb["avg_us"] * 1e-6
-        kernels[cls] = {"launches": counts[cls], "avg_us": kb["avg_us"],
-                        "est_share_s": counts[cls] * dur,
-                        "gbs": kb["bytes"] / dur / 1e9, "tflops": kb["flops"] / dur / 1e12,
-                        "fp64_issue_frac": kb["fp64_instr"] / dur / FP64_ISSUE_PEAK,
-                        "bytes": kb["bytes"], "flops": kb["flops"], "fp64_instr": kb["fp64_instr"]}
-    # ---- mixed precision on the same instance: time to T and error at T against FP64 ----
-    mixed = None
-    if not args.no_mixed:
-        y.copy_(y0)
-        ch.ch_integrate(G.h, prm["ee2"], y)
-        y_fp64 = y.clone()
-        Gm = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_MIXED, wl["mmax"], stream)
-        ym = torch.empty_like(y0)
-        ym.copy_(y0)
-        ch.ch_integrate(Gm.h, prm["ee2"], ym)            # warm-up (graph capture)
-        ym.copy_(y0)
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        stm = ch.ch_integrate(Gm.h, prm["ee2"], ym)
-        e1.record(stream); e1.synchronize()
-        ms_m = e0.elapsed_time(e1)
-        err = float(torch.linalg.norm(ym - y_fp64) / torch.linalg.norm(y_fp64))
-        mixed = {"ee2_ms_to_T": ms_m, "ee2_speedup_vs_fp64": ttt["ee2"]["ms"] / ms_m,
-                 "ee2_rel_err_at_T_vs_fp64": err, "steps": stm["steps"], "matvecs": stm["matvecs"],
-                 "ops_per_s": N * (stm["matvecs"] + stm["rhs_evals"]) / (ms_m * 1e-3),
-                 "mass_drift": float(abs(ym.mean() - y0.mean()))}
-        Gm.close()
-
-    # ---- end to end through the C ABI with host buffers ----------------------------------
-    e2e = None
-    if not args.no_e2e:
-        y_host = torch.from_numpy(y0_host.copy()).pin_memory()
-        out_host = torch.empty(N, dtype=torch.float64).pin_memory()
-        e2e_ops, e2e_ms = 0, 0.0
-        for k in range(max(1, args.steps // 2)):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for s in ("ee2", "lim"):
-                y.copy_(y_host, non_blocking=True)
-                st = ch.ch_integrate(G.h, prm[s], y)
-                out_host.copy_(y, non_blocking=True)
-                e2e_ops += N * (st["matvecs"] + st["rhs_evals"])
-            e1.record(stream)
-            e1.synchronize()
-            e2e_ms += e0.elapsed_time(e1)
-        e2e = {"value": e2e_ops / (e2e_ms * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": 2 * N * 8}
-
-    # ---- roofline: every streaming kernel class timed on the workload grid ---------------
-    # (CUDA events on the grid's stream around a graph of back-to-back launches); the
-    # dominant class is the one with the largest launches x mean duration in the timed region
-    kernels = {}
-    for cls in (() if args.no_roofline else ("tstage", "wstage", "mgs", "resid1", "lim2", "rhs1", "rhs2")):
+    classes = ("arnoldi", "tstage", "wstage", "mgs", "resid1", "lim2", "rhs1", "rhs2")
+    for cls in (() if args.no_roofline else classes):
+        if counts[cls] == 0:
+            continue                     # not launched in the timed region on this grid
         kb = ch.ch_bench_kernel(G.h, cls, 200)
         dur = kb["avg_us"] * 1e-6
         kernels[cls] = {"launches": counts[cls], "avg_us": kb["avg_us"],

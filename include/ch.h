@@ -182,6 +182,7 @@ typedef enum {
     CH_K_LIM2,          /* stage 2 fused with the LIM update (Fig. 1 steps 6/10) */
     CH_K_ENERGY,        /* energy and mass */
     CH_K_ARM,           /* Krylov start: beta, tol_phi (Eq. tol_phi) */
+    CH_K_ARNOLDI,       /* a whole Arnoldi iteration (Fig. 2 lines 4-9) in one launch */
     CH_K_COUNT
 } ch_kernel_class;
 
@@ -200,7 +201,8 @@ ch_status ch_timing_read(ch_grid *g, double *total_ms, int64_t *timed_launches,
  * launches captured in a CUDA graph, CUDA events on the grid's stream around the graph.
  * Returns the mean duration of one launch and its algorithmic traffic and arithmetic per
  * launch (bytes the kernel must move, floating-point operations counting an FMA as 2, and
- * issued FP64-pipe instructions for FP64 grids).  Supported classes: CH_K_TSTAGE,
+ * issued FP64-pipe instructions for FP64 grids).  Supported classes: CH_K_ARNOLDI (j = 10,
+ * on grids that run fused Arnoldi iterations), CH_K_TSTAGE,
  * CH_K_WSTAGE, CH_K_MGS, CH_K_RESID1, CH_K_LIM2, CH_K_RHS1, CH_K_RHS2.  Call after an
  * integration so the workspace holds finite data.  Synchronises.                         */
 ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us,

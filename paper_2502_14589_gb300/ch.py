@@ -74,7 +74,7 @@ _SIGS = {
 }
 
 KERNEL_CLASSES = ["prep", "tstage", "wstage", "mgs", "phi", "combine", "rhs1", "rhs2",
-                  "resid1", "resid2", "lim2", "energy", "arm"]
+                  "resid1", "resid2", "lim2", "energy", "arm", "arnoldi"]
 
 
 def lib_path() -> str:

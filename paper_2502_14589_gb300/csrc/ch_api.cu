@@ -73,8 +73,10 @@ struct ch_grid {
     int64_t launches;
     ch::Timing timing;
     cudaStream_t cap_stream;      // private non-blocking stream used only to capture graphs
-    std::map<std::tuple<int, const void *, int, int>, IterGraph> graphs;
+    std::map<std::tuple<int, const void *, int, int, int>, IterGraph> graphs;
     int use_graphs;
+    int fused_arnoldi;            // 1: one cooperative launch per Arnoldi iteration
+    int arn_blocks;               // its grid
     // device workspace
     double *D, *G, *t, *q;        // per-step coefficients and stage scratch
     double *F[2];                 // rhs buffers; F[cur] is basis column 0 of a Krylov run
@@ -84,6 +86,7 @@ struct ch_grid {
     float *Vf, *Wf[2], *Df, *tf;  // mixed precision: FP32 basis (slot 0 = Wf[cur]), D, stage
     double *H;                    // (mmax_cap + 1) x mmax_cap, row-major
     double *u;                    // mmax_cap
+    double *ub;                   // kPhiBlock x (mmax_cap + 1): u of each j of a phi block
     double *phi_scratch;
     double *partials;
     Ctrl *ctrl;
@@ -110,8 +113,11 @@ static ch_status sync_ctrl(ch_grid *g) {
         const int st = g->hctrl->status;
         int zero = 0;
         CUDA_TRY(cudaMemcpyAsync(&g->ctrl->status, &zero, sizeof(int), cudaMemcpyHostToDevice, g->stream));
+        if (st == CH_ETIMEOUT)   // a grid barrier gave up: its counters are no longer in step
+            CUDA_TRY(cudaMemsetAsync(&g->ctrl->bar, 0, sizeof g->ctrl->bar, g->stream));
         CUDA_TRY(cudaStreamSynchronize(g->stream));
         return fail((ch_status)st, st == CH_ENONFINITE ? "non-finite value in the solution or a reduction"
+                                   : st == CH_ETIMEOUT ? "a grid barrier of the Arnoldi iteration timed out"
                                                        : "Krylov run found no admissible step size");
     }
     return CH_OK;
@@ -163,32 +169,45 @@ static void rhs(ch_grid *g, const double *y, double *out, int eyre, int mode,
 // red[1] = ||g_hat||^2 when use_ghat).  Dm must hold the linearisation coefficients in the
 // basis precision VT.  The result y0 + V_j (beta u) is written to ynext (FP64); the run's
 // scalars are left in ctrl (not synchronised).
-// Kernels of Arnoldi iteration j (Fig. 2 lines 4-20) and the copy of the device `active`
-// flag to pinned memory, queued on L.stream.
+// Krylov dimensions evaluated together by one projected-phi launch (Fig. 2 lines 10-14 for
+// j0..j0+3 from the same H).  Iterations past the j at exit are speculative work: their
+// A_hat products are not counted as matvecs and their basis columns are never combined.
+constexpr int kPhiBlock = 4;
+
+// Kernels of Arnoldi iterations j0..j1 (Fig. 2 lines 4-9, 21), the projected phi and residual
+// tests of those dimensions, and the copy of the device `active` flag to pinned memory.
 template <typename VT>
-static void queue_iteration(ch_grid *g, const Launch &L, VT *slot0, VT *V, const VT *Dm, VT *t,
-                            int j, int mmax, cudaStream_t stream) {
+static void queue_block(ch_grid *g, const Launch &L, VT *slot0, VT *V, const VT *Dm, VT *t,
+                        int j0, int j1, int mmax, cudaStream_t stream) {
     const int ldh = g->mmax_cap;
     auto W = [&](int c) -> VT * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * g->ldv; };
-    VT *Wj = W(j), *Wn = W(j + 1);
-    ch::launch_tstage<VT>(L, g->g, Wj, Dm, t, 1);
-    ch::launch_wstage<VT>(L, g->g, t, Wn, slot0, &g->H[0 * ldh + (j - 1)], j - 1, 1);
-    for (int k = 1; k <= j; ++k) {
-        const int last = (k == j);
-        ch::launch_mgs<VT>(L, g->g.N, Wn, W(k), last ? nullptr : W(k + 1),
-                           &g->H[(k - 1) * ldh + (j - 1)], last ? nullptr : &g->H[k * ldh + (j - 1)],
-                           k, last);
+    for (int j = j0; j <= j1; ++j) {
+        if (g->fused_arnoldi) {
+            ch::launch_arnoldi<VT>(L, g->arn_blocks, g->g, slot0, V, g->ldv, Dm, t, g->H, ldh, j);
+            if (mmax > 63) ch::launch_phi(L, g->H, ldh, j, mmax, g->u, g->phi_scratch);
+            continue;
+        }
+        VT *Wj = W(j), *Wn = W(j + 1);
+        ch::launch_tstage<VT>(L, g->g, Wj, Dm, t, 1);
+        ch::launch_wstage<VT>(L, g->g, t, Wn, slot0, &g->H[0 * ldh + (j - 1)], j - 1, 1);
+        for (int k = 1; k <= j; ++k) {
+            const int last = (k == j);
+            ch::launch_mgs<VT>(L, g->g.N, Wn, W(k), last ? nullptr : W(k + 1),
+                               &g->H[(k - 1) * ldh + (j - 1)], last ? nullptr : &g->H[k * ldh + (j - 1)],
+                               k, last, ldh);
+        }
+        if (mmax > 63) ch::launch_phi(L, g->H, ldh, j, mmax, g->u, g->phi_scratch);
     }
-    ch::launch_phi(L, g->H, ldh, j, mmax, g->u, g->phi_scratch);
-    cudaMemcpyAsync(&g->hflag[j & 1], &g->ctrl->active, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (mmax <= 63) ch::launch_phi_block(L, g->H, ldh, j0, j1, mmax, g->u, g->ub, g->mmax_cap + 1);
+    cudaMemcpyAsync(&g->hflag[j1 & 1], &g->ctrl->active, sizeof(int), cudaMemcpyDeviceToHost, stream);
 }
 
-// The iteration as a CUDA graph, captured on the private stream the first time this
-// (precision, start column, j, m_max) occurs and replayed afterwards.
+// The block as a CUDA graph, captured on the private stream the first time this
+// (precision, start column, j0, j1, m_max) occurs and replayed afterwards.
 template <typename VT>
-static ch_status iteration_graph(ch_grid *g, VT *slot0, VT *V, const VT *Dm, VT *t, int j,
-                                 int mmax, IterGraph **out) {
-    auto key = std::make_tuple((int)sizeof(VT), (const void *)slot0, j, mmax);
+static ch_status block_graph(ch_grid *g, VT *slot0, VT *V, const VT *Dm, VT *t, int j0, int j1,
+                             int mmax, IterGraph **out) {
+    auto key = std::make_tuple((int)sizeof(VT), (const void *)slot0, j0, j1, mmax);
     auto it = g->graphs.find(key);
     if (it != g->graphs.end()) { *out = &it->second; return CH_OK; }
     IterGraph ig;
@@ -199,9 +218,9 @@ static ch_status iteration_graph(ch_grid *g, VT *slot0, VT *V, const VT *Dm, VT 
     Lc.timing = &counter;
     cudaGraph_t graph;
     CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
-    queue_iteration<VT>(g, Lc, slot0, V, Dm, t, j, mmax, g->cap_stream);
+    queue_block<VT>(g, Lc, slot0, V, Dm, t, j0, j1, mmax, g->cap_stream);
     cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
-    if (e != cudaSuccess) return fail(CH_ECUDA, "graph capture of iteration %d: %s", j, cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(CH_ECUDA, "graph capture of iterations %d-%d: %s", j0, j1, cudaGetErrorString(e));
     e = cudaGraphInstantiate(&ig.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(CH_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
@@ -212,8 +231,8 @@ static ch_status iteration_graph(ch_grid *g, VT *slot0, VT *V, const VT *Dm, VT 
 
 // One Krylov run of Fig. 2.  Basis column W_1 is in slot0 and red[0] = ||W_1||^2 (and
 // red[1] = ||g_hat||^2 when use_ghat).  Dm must hold the linearisation coefficients in the
-// basis precision VT.  The iteration loop is left with the run's scalars in ctrl; the
-// caller queues the combine.  Iteration j+1 is queued before iteration j's flag is read.
+// basis precision VT.  The run's scalars are left in ctrl; the caller queues the combine.
+// Block b+1 is queued before block b's flag is read, so the GPU never waits on the host.
 template <typename VT>
 static ch_status krylov_run_t(ch_grid *g, const double *y0, VT *slot0, VT *V, const VT *Dm,
                               VT *t, double tau0, double tol_phi_fixed, double tol, int use_ghat,
@@ -222,22 +241,30 @@ static ch_status krylov_run_t(ch_grid *g, const double *y0, VT *slot0, VT *V, co
     const Launch &L = g->L;
     ch::launch_krylov_arm(L, tau0, tol_phi_fixed, tol, use_ghat);
     const bool graphs = g->use_graphs && g->timing.cls < 0;
-    for (int j = 1; j <= mmax; ++j) {
-        if (graphs) {
-            IterGraph *ig;
-            CH_TRY(iteration_graph<VT>(g, slot0, V, Dm, t, j, mmax, &ig));
+    const int B = mmax <= 63 ? kPhiBlock : 1;
+    int prev_j1 = 0;
+    for (int j0 = 1; j0 <= mmax; j0 += B) {
+        const int j1 = std::min(j0 + B - 1, mmax);
+        IterGraph *ig = nullptr;
+        if (graphs && block_graph<VT>(g, slot0, V, Dm, t, j0, j1, mmax, &ig) != CH_OK) {
+            cudaGetLastError();               // capture not possible here: launch directly
+            g->use_graphs = 0;
+            ig = nullptr;
+        }
+        if (ig) {
             CUDA_TRY(cudaGraphLaunch(ig->exec, g->stream));
             g->launches += ig->launches;
             for (int k = 0; k < CH_K_COUNT; ++k) g->timing.counts[k] += ig->counts[k];
         } else {
-            queue_iteration<VT>(g, L, slot0, V, Dm, t, j, mmax, g->stream);
+            queue_block<VT>(g, L, slot0, V, Dm, t, j0, j1, mmax, g->stream);
         }
         CH_TRY(check_launch());
-        CUDA_TRY(cudaEventRecord(g->ev[j & 1], g->stream));
-        if (j >= 2) {
-            CUDA_TRY(cudaEventSynchronize(g->ev[(j - 1) & 1]));
-            if (g->hflag[(j - 1) & 1] == 0) break;
+        CUDA_TRY(cudaEventRecord(g->ev[j1 & 1], g->stream));
+        if (prev_j1 > 0) {
+            CUDA_TRY(cudaEventSynchronize(g->ev[prev_j1 & 1]));
+            if (g->hflag[prev_j1 & 1] == 0) break;
         }
+        prev_j1 = j1;
     }
     return CH_OK;
 }
@@ -437,6 +464,8 @@ ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us
                           double *bytes_per_launch, double *flops_per_launch,
                           double *fp64_instr_per_launch) {
     if (!g || reps < 1 || reps > 100000) return fail(CH_EINVAL, "bad arguments");
+    if (kernel_class == CH_K_ARNOLDI && !g->fused_arnoldi)
+        return fail(CH_EINVAL, "this grid runs Arnoldi iterations as separate kernels");
     const int d = g->g.dim;
     const double N = (double)g->g.N;
     const bool mixed = g->precision == CH_MIXED;
@@ -466,8 +495,8 @@ ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us
             bytes = 3 * vb * N; flops = (3 + 3.0 * d) * N; instr = mixed ? 0 : (2 + 2.0 * d) * N;
             break;
         case CH_K_MGS:      // w -= c v_k, dot(w, v_{k+1}): 2 fma
-            if (mixed) ch::launch_mgs<float>(Lc, g->g.N, g->Vf, g->Wf[0], g->Wf[1], &g->H[0], &g->H[1], 1, 0);
-            else ch::launch_mgs<double>(Lc, g->g.N, g->V, g->F[0], g->F[1], &g->H[0], &g->H[1], 1, 0);
+            if (mixed) ch::launch_mgs<float>(Lc, g->g.N, g->Vf, g->Wf[0], g->Wf[1], &g->H[0], &g->H[1], 1, 0, 0);
+            else ch::launch_mgs<double>(Lc, g->g.N, g->V, g->F[0], g->F[1], &g->H[0], &g->H[1], 1, 0, 0);
             bytes = 4 * vb * N; flops = 4.0 * N; instr = mixed ? 0 : 2.0 * N;
             break;
         case CH_K_RESID1:   // t = G - D x + sum kap (pairs): fma + d (add + fma)
@@ -486,6 +515,15 @@ ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us
             ch::launch_rhs2(Lc, g->g, g->t, nullptr, g->y[1], nullptr, nullptr, g->y[2], 0.0, 1);
             bytes = 16.0 * N; flops = (3 + 3.0 * d) * N; instr = (2 + 2.0 * d) * N;
             break;
+        case CH_K_ARNOLDI: {  // one whole Arnoldi iteration with j = min(10, capacity) passes
+            const int j = std::min(10, g->mmax_cap);
+            if (mixed) ch::launch_arnoldi<float>(Lc, g->arn_blocks, g->g, g->Wf[0], g->Vf, g->ldv, g->Df, g->tf, g->H, g->mmax_cap, j);
+            else ch::launch_arnoldi<double>(Lc, g->arn_blocks, g->g, g->F[0], g->V, g->ldv, g->D, g->t, g->H, g->mmax_cap, j);
+            bytes = (6 + 4.0 * j) * vb * N;
+            flops = ((1 + 3.0 * d) + (3 + 3.0 * d) + 4.0 * j) * N;
+            instr = mixed ? 0 : ((1 + 2.0 * d) + (2 + 2.0 * d) + 2.0 * j) * N;
+            break;
+        }
         default:
             cudaStreamEndCapture(g->cap_stream, &graph);
             return fail(CH_EINVAL, "kernel class %d cannot be benchmarked", kernel_class);
@@ -575,6 +613,8 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
     {
         const char *env = getenv("CH_NO_GRAPHS");
         g->use_graphs = !(env && env[0] == '1');
+        env = getenv("CH_NO_FUSED_ARNOLDI");
+        g->fused_arnoldi = !(env && env[0] == '1');
     }
 
     auto cleanup_fail = [&](ch_status st, const char *what, cudaError_t e) {
@@ -587,6 +627,9 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
     if (e != cudaSuccess) return cleanup_fail(CH_ECUDA, "device query", e);
     const int64_t want = (N + ch::kThreads - 1) / ch::kThreads;
     g->L.blocks = (int)std::min<int64_t>(want, (int64_t)sms * ch::kBlocksPerSM);
+    g->arn_blocks = precision == CH_MIXED ? ch::arnoldi_blocks<float>(dim, N)
+                                          : ch::arnoldi_blocks<double>(dim, N);
+    if (g->arn_blocks < 1) g->fused_arnoldi = 0;
     g->L.stream = g->stream;
     g->L.launches = &g->launches;
     g->L.timing = &g->timing;
@@ -600,8 +643,9 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
         {&g->V, vb * (size_t)mmax_capacity},
         {&g->H, sizeof(double) * (size_t)(mmax_capacity + 1) * mmax_capacity},
         {&g->u, sizeof(double) * (size_t)(mmax_capacity + 1)},
+        {&g->ub, sizeof(double) * (size_t)kPhiBlock * (mmax_capacity + 1)},
         {&g->phi_scratch, sizeof(double) * (size_t)(6 * (mmax_capacity + 1) * (mmax_capacity + 1) + 2 * (mmax_capacity + 1))},
-        {&g->partials, sizeof(double) * ch::kMaxRed * (size_t)g->L.blocks},
+        {&g->partials, sizeof(double) * (size_t)std::max(ch::kMaxRed * g->L.blocks, 2 * g->arn_blocks)},
     };
     for (auto &a : allocs) {
         if (precision == CH_MIXED && a.p == &g->V) continue;     // FP32 basis instead
@@ -639,7 +683,7 @@ ch_status ch_destroy_grid(ch_grid *g) {
     if (!g) return CH_OK;
     cudaStreamSynchronize(g->stream);
     double *bufs[] = {g->D, g->G, g->t, g->q, g->F[0], g->F[1], g->y[0], g->y[1], g->y[2],
-                      g->V, g->H, g->u, g->phi_scratch, g->partials};
+                      g->V, g->H, g->u, g->ub, g->phi_scratch, g->partials};
     for (double *b : bufs)
         if (b) cudaFree(b);
     float *fbufs[] = {g->Vf, g->Wf[0], g->Wf[1], g->Df, g->tf};

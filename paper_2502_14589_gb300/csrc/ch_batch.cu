@@ -341,8 +341,10 @@ kb_mgs(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, VT *__restrict__ w,
             acc.add(r, r);
         }
         double v[1] = {acc.value()};
-        inst_sum<1>(v, I, ck.inst, partials, nct, tickets,
-                    [&](double (&tot)[1]) { ctrl->hnext2 = tot[0]; });
+        inst_sum<1>(v, I, ck.inst, partials, nct, tickets, [&](double (&tot)[1]) {
+            ctrl->hnext2 = tot[0];
+            H[j * ldh + (j - 1)] = sqrt(tot[0]);          // Fig. 2 line 9
+        });
     }
 }
 

@@ -57,7 +57,9 @@ struct Ctrl {
     double gam[130];    // v_c = gam[c-1] W_c: scale of each stored (unnormalised) basis vector
     double coef[130];   // beta gam_c u_c: coefficients of Fig. 2 line 23
     double vmean[130];  // mean of each basis vector (mixed-precision mass correction)
+    double resj[130];   // resnorm(tau0) of Krylov dimension j (block-parallel phi)
     unsigned int ticket[8];
+    alignas(128) unsigned long long bar;   // grid-barrier arrivals (own cache line)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -207,8 +209,16 @@ template <typename VT>
 void launch_wstage(const Launch &L, const Geom &g, const VT *t, VT *w, const VT *v1,
                    double *hout, int jm1, int guarded);
 template <typename VT>
-void launch_mgs(const Launch &L, int64_t N, VT *w, const VT *vk, const VT *vk1, const double *hk,
-                double *hout, int k, int last);
+void launch_mgs(const Launch &L, int64_t N, VT *w, const VT *vk, const VT *vk1, double *hk,
+                double *hout, int k, int last, int ldh_next);
+// Whole Arnoldi iteration j in one cooperative launch of `blocks` blocks (grid barriers
+// between passes; L.partials must hold 2 x blocks doubles).  arnoldi_blocks gives the grid
+// for N points: at most the number of blocks that can be resident at once, 0 if none.
+template <typename VT>
+void launch_arnoldi(const Launch &L, int blocks, const Geom &g, VT *slot0, VT *V, int64_t ldv,
+                    const VT *D, VT *t, double *H, int ldh, int j);
+template <typename VT>
+int arnoldi_blocks(int dim, int64_t N);
 void launch_combine32(const Launch &L, int64_t N, const double *y0, const float *v0,
                       const float *V, int64_t ldv, float *d, double *ynext);
 void launch_to32(const Launch &L, int64_t N, const double *x, float *y);
@@ -232,6 +242,11 @@ void launch_krylov_arm(const Launch &L, double tau0, double tol_phi_fixed, doubl
 int phi_setup();
 void launch_phi(const Launch &L, double *H, int ldh, int j, int mmax, double *u,
                 double *scratch);
+// Block-parallel projected phi for Krylov dimensions j0..j1 (Fig. 2 lines 10-14 for each j
+// from the same H), then the decision: the first j whose residual test passes ends the run;
+// with none and j1 == mmax the step trace of lines 15-19 runs at mmax.
+void launch_phi_block(const Launch &L, double *H, int ldh, int j0, int j1, int mmax, double *u,
+                      double *ub, int ldu);
 // Batched projected phi: one 8-CTA cluster per instance, j + 1 <= 64.
 void launch_phi_batch(const Launch &L, Ctrl *ctrls, double *Hs, int64_t hstride, double *us,
                       int64_t ustride, int ldh, int j, int mmax, int count);

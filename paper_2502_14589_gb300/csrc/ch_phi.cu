@@ -44,7 +44,7 @@ struct PhiWork {
 // C = A B on one thread block.
 struct MatmulBlock {
     __device__ __forceinline__ void operator()(int n, const double *A, const double *B,
-                                               double *C) const {
+                                               double *C, bool pre = false) const {
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             const int r = e / n, c = e - r * n;
             double acc = 0.0;
@@ -57,17 +57,18 @@ struct MatmulBlock {
 
 // C = A B on a cluster: every CTA holds the same copies of A and B in its shared memory,
 // computes a slice of rows of C and stores it into the C of every CTA of the cluster
-// (distributed shared memory).  Cluster barriers before (nobody still reads C) and after
-// (all slices arrived).
+// (distributed shared memory).  A cluster barrier after the product (all slices arrived);
+// with `pre` also one before it, for the products whose C another CTA may still be reading
+// in the preceding local phase (the first product of an exponential and its first squaring).
 struct MatmulCluster {
     __device__ __forceinline__ void operator()(int n, const double *A, const double *B,
-                                               double *C) const {
+                                               double *C, bool pre = false) const {
         cg::cluster_group cl = cg::this_cluster();
         const int rank = (int)cl.block_rank(), nr = (int)cl.num_blocks();
         const int r0 = rank * n / nr, r1 = (rank + 1) * n / nr;
         double *dst[kPhiCluster];
         for (int q = 0; q < nr; ++q) dst[q] = cl.map_shared_rank(C, q);
-        cl.sync();
+        if (pre) cl.sync();
         for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
             const int r = r0 + e / n, c = e - (r - r0) * n;
             double acc = 0.0;
@@ -103,7 +104,7 @@ __device__ double *expm_block(int n, PhiWork &W, const MM &mm) {
     const double scale = ldexp(1.0, -sq);
     for (int e = threadIdx.x; e < nn; e += blockDim.x) X[e] *= scale;
     __syncthreads();
-    mm(n, X, X, X2);
+    mm(n, X, X, X2, true);     // another CTA may still be in the previous exponential
     mm(n, X2, X2, X4);
     mm(n, X4, X2, X6);
     const double *c = W.c;
@@ -181,7 +182,7 @@ __device__ double *expm_block(int n, PhiWork &W, const MM &mm) {
         if (sq < 64) W.chain[sq] = R[(n - 2) * n + (n - 1)];
     }
     for (int k = 0; k < sq; ++k) {
-        mm(n, R, R, S);
+        mm(n, R, R, S, k == 0);   // the P, Q step above still reads X6 (= S) in other CTAs
         double *t = R; R = S; S = t;
         if (threadIdx.x == 0 && sq - k - 1 < 64) W.chain[sq - k - 1] = R[(n - 2) * n + (n - 1)];
     }
@@ -233,7 +234,7 @@ __device__ void phi_step(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double
             W.c[k] = W.c[k - 1] * (double)(13 - k + 1) / ((double)(2 * 13 - k + 1) * k);
     }
     __syncthreads();
-    const double hnext = sqrt(ctrl->hnext2);             // Fig. 2 line 9
+    const double hnext = H[j * ldh + (j - 1)];           // Fig. 2 line 9 (last MGS pass)
     const double tau0 = ctrl->tau0, tol = ctrl->tol_phi;
     double *uo = writer ? u : nullptr;
     int evals = 1;
@@ -368,6 +369,105 @@ k_phi_batch(Ctrl *ctrls, double *Hs, int64_t hstride, double *us, int64_t ustrid
              MatmulCluster(), true);
 }
 
+// ---- block-parallel evaluation: resnorm(tau0) and u for one Krylov dimension j -------------
+template <typename MM>
+__device__ void phi_eval_only(Ctrl *ctrl, const double *H, int ldh, int j, double *ub_j,
+                              double *base, bool writer, const MM &mm) {
+    __shared__ PhiWork W;
+    const int n = j + 1;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k) W.b[k] = base + (size_t)k * n * n;
+        W.fcol = base + (size_t)6 * n * n;
+        W.colsum = W.fcol + n;
+        for (int k = 0; k < kTraceSlots; ++k) W.slot[k] = nullptr;
+        W.cur = W.tmp = nullptr;
+        W.c[0] = 1.0;
+        for (int k = 1; k <= 13; ++k)
+            W.c[k] = W.c[k - 1] * (double)(13 - k + 1) / ((double)(2 * 13 - k + 1) * k);
+    }
+    __syncthreads();
+    const double hnext = H[j * ldh + (j - 1)];
+    const double res = phi_eval(j, H, ldh, hnext, ctrl->tau0, writer ? ub_j : nullptr, W, mm);
+    if (writer && threadIdx.x == 0) ctrl->resj[j] = (isfinite(hnext) && isfinite(res)) ? res : NAN;
+}
+
+__global__ void __launch_bounds__(kPhiThreads)
+k_phi_multi_cluster(Ctrl *ctrl, const double *H, int ldh, int j0, double *ub, int ldu) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int c = (int)(blockIdx.x / cl.num_blocks());
+    if (!ctrl->active) return;
+    extern __shared__ double smem[];
+    phi_eval_only(ctrl, H, ldh, j0 + c, ub + (size_t)c * ldu, smem, cl.block_rank() == 0,
+                  MatmulCluster());
+}
+
+__global__ void __launch_bounds__(kPhiThreads)
+k_phi_multi_block(Ctrl *ctrl, const double *H, int ldh, int j0, double *ub, int ldu) {
+    if (!ctrl->active) return;
+    extern __shared__ double smem[];
+    phi_eval_only(ctrl, H, ldh, j0 + (int)blockIdx.x, ub + (size_t)blockIdx.x * ldu, smem, true,
+                  MatmulBlock());
+}
+
+// First j in [j0, jlast] whose residual test passed (Fig. 2 lines 13-14): that j ends the
+// run, exactly as the per-iteration test would; a non-finite residual first ends it with an
+// error.  Returns true when the run ended.
+__device__ bool decide_first(Ctrl *ctrl, int j0, int jlast, const double *ub, int ldu,
+                             bool writer) {
+    __shared__ int dj;
+    if (threadIdx.x == 0) {
+        dj = 0;
+        for (int j = j0; j <= jlast; ++j) {
+            const double r = ctrl->resj[j];
+            if (!isfinite(r)) { dj = -1; break; }
+            if (r <= ctrl->tol_phi) { dj = j; break; }
+        }
+    }
+    __syncthreads();
+    const int d = dj;
+    if (d == 0) return false;
+    if (writer) {
+        if (threadIdx.x == 0) {
+            ctrl->phi_evals += (d > 0 ? d : jlast) - j0 + 1;
+            ctrl->active = 0;
+            if (d < 0) {
+                ctrl->status = CH_ENONFINITE;
+                ctrl->jexit = 0;
+            } else {
+                ctrl->jexit = d;
+                ctrl->tau = ctrl->tau0;
+                ctrl->converged = 1;
+                ctrl->shrunk = 0;
+                ctrl->resnorm = ctrl->resj[d];
+            }
+        }
+        if (d > 0)
+            for (int c = threadIdx.x; c < d; c += blockDim.x)
+                ctrl->coef[c] = ctrl->beta * ctrl->gam[c] * ub[(size_t)(d - j0) * ldu + c];  // line 23
+    }
+    __syncthreads();
+    return true;
+}
+
+__global__ void k_phi_decide(Ctrl *ctrl, int j0, int j1, const double *ub, int ldu) {
+    if (!ctrl->active) return;
+    if (!decide_first(ctrl, j0, j1, ub, ldu, true) && threadIdx.x == 0)
+        ctrl->phi_evals += j1 - j0 + 1;
+}
+
+// Last block of the run (j1 == mmax): decide among j0..mmax-1, else Fig. 2 at mmax with the
+// step trace (the evaluation at tau0 is repeated to obtain its squaring chain).
+__global__ void __launch_bounds__(kPhiThreads)
+k_phi_decide_trace(Ctrl *ctrl, double *H, int ldh, int j0, int mmax, double *u, const double *ub,
+                   int ldu) {
+    if (!ctrl->active) return;
+    extern __shared__ double smem[];
+    const bool writer = cg::this_cluster().block_rank() == 0;
+    if (j0 < mmax && decide_first(ctrl, j0, mmax - 1, ub, ldu, writer)) return;
+    if (writer && threadIdx.x == 0) ctrl->phi_evals += mmax - j0;
+    phi_step(ctrl, H, ldh, mmax, mmax, u, smem, writer, MatmulCluster(), true);
+}
+
 // Dynamic shared memory of one phi launch: six work matrices and two vectors, plus the
 // trace matrices when j == mmax and n <= 32.
 static size_t phi_smem_bytes(int n, int j, int mmax) {
@@ -383,6 +483,12 @@ int phi_setup() {
         e = cudaFuncSetAttribute(k_phi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_phi_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_phi_multi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_phi_multi_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_phi_decide_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     return (int)e;
 }
 
@@ -412,6 +518,50 @@ void launch_phi(const Launch &L, double *H, int ldh, int j, int mmax, double *u,
     const int use_smem = n <= kPhiSmemMaxN;
     const size_t bytes = use_smem ? phi_smem_bytes(n, j, mmax) : 0;
     k_phi<<<1, kPhiThreads, bytes, L.stream>>>(L.ctrl, H, ldh, j, mmax, u, scratch, use_smem);
+}
+
+static void launch_cluster(const void *fn, int clusters, size_t bytes, cudaStream_t st, void **args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kPhiCluster * clusters, 1, 1);
+    cfg.blockDim = dim3(kPhiThreads, 1, 1);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kPhiCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+void launch_phi_block(const Launch &L, double *H, int ldh, int j0, int j1, int mmax, double *u,
+                      double *ub, int ldu) {
+    const int nj = j1 - j0 + 1;
+    const int n1 = j1 + 1;
+    {
+        LaunchScope scope(L, CH_K_PHI);
+        const size_t bytes = (size_t)(6 * n1 * n1 + 2 * n1) * sizeof(double);
+        if (n1 <= 8) {
+            k_phi_multi_block<<<nj, kPhiThreads, bytes, L.stream>>>(L.ctrl, H, ldh, j0, ub, ldu);
+        } else {
+            Ctrl *c = L.ctrl;
+            const double *Hc = H;
+            void *args[] = {&c, &Hc, &ldh, &j0, &ub, &ldu};
+            launch_cluster((const void *)k_phi_multi_cluster, nj, bytes, L.stream, args);
+        }
+    }
+    LaunchScope scope(L, CH_K_PHI);
+    if (j1 < mmax) {
+        k_phi_decide<<<1, 128, 0, L.stream>>>(L.ctrl, j0, j1, ub, ldu);
+    } else {
+        Ctrl *c = L.ctrl;
+        const double *ubc = ub;
+        void *args[] = {&c, &H, &ldh, &j0, &mmax, &u, &ubc, &ldu};
+        launch_cluster((const void *)k_phi_decide_trace, 1, phi_smem_bytes(mmax + 1, mmax, mmax),
+                       L.stream, args);
+    }
 }
 
 void launch_phi_batch(const Launch &L, Ctrl *ctrls, double *Hs, int64_t hstride, double *us,

@@ -191,8 +191,8 @@ __device__ __forceinline__ float &lane(float4 &v, int k) {
 template <typename VT>
 __global__ void __launch_bounds__(kThreads)
 k_mgs(int64_t N, VT *__restrict__ w, const VT *__restrict__ vk, const VT *__restrict__ vk1,
-      const double *hk, double *hout, int k, int last, double *partials, unsigned int *ticket,
-      Ctrl *ctrl) {
+      double *hk, double *hout, int k, int last, int ldh_next, double *partials,
+      unsigned int *ticket, Ctrl *ctrl) {
     if (!ctrl->active) return;
     typedef typename Vec16<VT>::T V;
     constexpr int WD = Vec16<VT>::W;
@@ -222,9 +222,204 @@ k_mgs(int64_t N, VT *__restrict__ w, const VT *__restrict__ vk, const VT *__rest
     double tot1[1] = {acc.value()};
     if (!last)
         grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { *hout = ctrl->gam[k] * tot[0]; });
-    else
-        grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { ctrl->hnext2 = tot[0]; });
+    else   // Fig. 2 lines 9 and 21: h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
+        grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) {
+            ctrl->hnext2 = tot[0];
+            const double h = sqrt(tot[0]);
+            hk[ldh_next] = h;
+            ctrl->gam[k] = 1.0 / h;
+        });
 }
+
+// ---------------------------------------------------------------------------------------
+// One whole Arnoldi iteration j (Fig. 2 lines 4-9 and the scale of line 21) in one
+// cooperative launch of one 1024-thread block per SM: t-stage, w-stage with h_{1j}, then
+// the j modified Gram-Schmidt passes, separated by grid barriers.  After each barrier every
+// block adds the per-block partials in block order itself (the same value in every block,
+// no serialised tail); partial buffers alternate between rounds, so a fast block never
+// overwrites sums a slow block is still reading.
+// ---------------------------------------------------------------------------------------
+constexpr int kArnThreads = 1024;
+constexpr long long kBarrierSpinLimit = 1ll << 24;     // ~1 s of short sleeps
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier on a monotonic arrival counter.  The counter starts at 0 and every launch
+// adds the grid size once per barrier, so it is a multiple of the grid size between
+// launches and arrival number `old` belongs to the round ending at (old / G + 1) G.  One
+// atomic per block; waiting blocks poll with acquire loads (no read-modify-write traffic on
+// the line the arrivals use).  The wait is bounded: on timeout the block records CH_ETIMEOUT
+// and goes on, so the kernel always ends and the host reports the failure (and clears the
+// counter).
+__device__ __forceinline__ void grid_barrier(unsigned long long *bar, int *status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long G = gridDim.x;
+        __threadfence();
+        const unsigned long long old = atomicAdd(bar, 1ull);
+        const unsigned long long target = (old / G + 1ull) * G;
+        long long spins = 0;
+        while (ld_acquire(bar) < target) {
+            if (++spins > kBarrierSpinLimit) { *status = CH_ETIMEOUT; break; }
+            __nanosleep(32);
+        }
+    }
+    __syncthreads();
+}
+
+// Sum of one value per thread of a kArnThreads block, valid in thread 0.  FP64 adds issue
+// at 2 lanes/clk/SM, so the tree is spread over four warps (one per SM sub-partition), each
+// adding 256 values from shared memory and finishing with a shuffle tree; thread 0 adds the
+// four in order.  sh holds kArnThreads + 8 doubles.
+__device__ __forceinline__ double arn_block_sum(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wid < 4) {
+        double a = 0.0;
+#pragma unroll
+        for (int r = 0; r < kArnThreads / 128; ++r) a += sh[wid * (kArnThreads / 4) + r * 32 + lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) sh[kArnThreads + wid] = a;
+    }
+    __syncthreads();
+    return ((sh[kArnThreads] + sh[kArnThreads + 1]) + sh[kArnThreads + 2]) + sh[kArnThreads + 3];
+}
+
+// Sum of the per-block partials in block order by one warp; every thread of every block
+// gets the same value.
+__device__ __forceinline__ double arn_grid_sum(const double *part, double *sh) {
+    if (threadIdx.x < 32) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) a += __ldcg(&part[b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (threadIdx.x == 0) sh[kArnThreads + 4] = a;
+    }
+    __syncthreads();
+    return sh[kArnThreads + 4];
+}
+
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kArnThreads, 1)
+k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const VT *__restrict__ D,
+          VT *__restrict__ t, double *H, int ldh, int j, double *partials, Ctrl *ctrl) {
+    if (!ctrl->active) return;                  // same value in every block
+    __shared__ double sh[kArnThreads + 8];
+    auto W = [&](int c) -> VT * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * ldv; };
+    unsigned long long *bar = &ctrl->bar;
+    const unsigned N = (unsigned)g.N;
+    const unsigned G = gridDim.x;
+    const VT *x = W(j);
+    VT *w = W(j + 1);
+    const VT *v1 = W(1);
+    // ---- stage 1: t = D (.) x - sum_a kap_a (x_{+a} + x_{-a})
+    {
+        const VT k0 = (VT)g.kap[0], k1 = (VT)g.kap[1], k2 = (VT)g.kap[2];
+        GRID_LOOP2(N, {
+            VT ps[3];
+            pair_sums<DIM>(g, x, i, ps);
+            VT acc = D[i] * x[i];
+            acc = fma(-k0, ps[0], acc);
+            acc = fma(-k1, ps[1], acc);
+            if (DIM == 3) acc = fma(-k2, ps[2], acc);
+            t[i] = acc;
+        })
+    }
+    grid_barrier(bar, &ctrl->status);
+    // ---- stage 2: w = gam_j (sigma t - sum_a s_a (t_{+a} + t_{-a})), partial w . W_1
+    {
+        const double gam = ctrl->gam[j - 1];
+        const VT c0 = (VT)(gam * g.sigma), c1 = (VT)(gam * g.s[0]), c2 = (VT)(gam * g.s[1]),
+                 c3 = (VT)(gam * g.s[2]);
+        DotAcc<VT> acc;
+        GRID_LOOP2(N, {
+            VT ps[3];
+            pair_sums<DIM>(g, t, i, ps);
+            VT r = c0 * t[i];
+            r = fma(-c1, ps[0], r);
+            r = fma(-c2, ps[1], r);
+            if (DIM == 3) r = fma(-c3, ps[2], r);
+            w[i] = r;
+            acc.add(r, v1[i]);
+        })
+        const double bsum = arn_block_sum(acc.value(), sh);
+        if (threadIdx.x == 0) partials[G + blockIdx.x] = bsum;
+    }
+    grid_barrier(bar, &ctrl->status);
+    double h = ctrl->gam[0] * arn_grid_sum(partials + G, sh);     // h_{1j}
+    if (blockIdx.x == 0 && threadIdx.x == 0) H[0 * ldh + (j - 1)] = h;
+    // ---- modified Gram-Schmidt passes k = 1..j (lines 5-8) and the norm of line 9
+    for (int k = 1; k <= j; ++k) {
+        const bool last = (k == j);
+        const VT c = (VT)(h * ctrl->gam[k - 1]);
+        const VT *vk = W(k), *vk1 = last ? W(k) : W(k + 1);
+        double *part = partials + (size_t)((k + 1) & 1) * G;       // round k + 1
+        DotAcc<VT> acc;
+        GRID_LOOP2(N, {
+            const VT r = fma(-c, vk[i], w[i]);
+            w[i] = r;
+            acc.add(r, last ? r : vk1[i]);
+        })
+        const double bsum = arn_block_sum(acc.value(), sh);
+        if (threadIdx.x == 0) part[blockIdx.x] = bsum;
+        grid_barrier(bar, &ctrl->status);
+        const double sum = arn_grid_sum(part, sh);
+        if (!last) {
+            h = ctrl->gam[k] * sum;                               // h_{k+1,j}
+            if (blockIdx.x == 0 && threadIdx.x == 0) H[k * ldh + (j - 1)] = h;
+        } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const double hn = sqrt(sum);                          // h_{j+1,j}
+            ctrl->hnext2 = sum;
+            H[j * ldh + (j - 1)] = hn;
+            ctrl->gam[j] = 1.0 / hn;
+        }
+    }
+}
+
+template <typename VT>
+int arnoldi_blocks(int dim, int64_t N) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dim == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<3, VT>, kArnThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<2, VT>, kArnThreads, 0);
+    const int64_t want = (N + 2 * kArnThreads - 1) / (2 * kArnThreads);
+    return (int)std::min<int64_t>(want, (int64_t)per_sm * sms);
+}
+template int arnoldi_blocks<double>(int, int64_t);
+template int arnoldi_blocks<float>(int, int64_t);
+
+template <typename VT>
+void launch_arnoldi(const Launch &L, int blocks, const Geom &g, VT *slot0, VT *V, int64_t ldv,
+                    const VT *D, VT *t, double *H, int ldh, int j) {
+    LaunchScope scope(L, CH_K_ARNOLDI);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks, 1, 1);
+    cfg.blockDim = dim3(kArnThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    Ctrl *ctrl = L.ctrl;
+    double *partials = L.partials;
+    if (g.dim == 3)
+        cudaLaunchKernelEx(&cfg, k_arnoldi<3, VT>, g, slot0, V, ldv, D, t, H, ldh, j, partials, ctrl);
+    else
+        cudaLaunchKernelEx(&cfg, k_arnoldi<2, VT>, g, slot0, V, ldv, D, t, H, ldh, j, partials, ctrl);
+}
+template void launch_arnoldi<double>(const Launch &, int, const Geom &, double *, double *, int64_t,
+                                     const double *, double *, double *, int, int);
+template void launch_arnoldi<float>(const Launch &, int, const Geom &, float *, float *, int64_t,
+                                    const float *, float *, double *, int, int);
 
 // ---------------------------------------------------------------------------------------
 // Fig. 2 line 23: y_next = y0 + V_j (beta u) = y0 + sum_c coef_c W_c, coef_c = beta gam_c u_c.
@@ -519,20 +714,22 @@ void launch_wstage(const Launch &L, const Geom &g, const VT *t, VT *w, const VT 
                    &L.ctrl->ticket[0], L.ctrl, guarded);
 }
 
+// hk points at H[k-1][j-1]; with `last` (k == j) the pass also stores h_{j+1,j} at
+// hk + ldh_next (= H[j][j-1], ldh_next = ldh) and gam[j] = 1/h_{j+1,j}.
 template <typename VT>
-void launch_mgs(const Launch &L, int64_t N, VT *w, const VT *vk, const VT *vk1, const double *hk,
-                double *hout, int k, int last) {
+void launch_mgs(const Launch &L, int64_t N, VT *w, const VT *vk, const VT *vk1, double *hk,
+                double *hout, int k, int last, int ldh_next) {
     LaunchScope scope(L, CH_K_MGS);
-    k_mgs<VT><<<L.blocks, kThreads, 0, L.stream>>>(N, w, vk, vk1, hk, hout, k, last, L.partials,
-                                                    &L.ctrl->ticket[0], L.ctrl);
+    k_mgs<VT><<<L.blocks, kThreads, 0, L.stream>>>(N, w, vk, vk1, hk, hout, k, last, ldh_next,
+                                                    L.partials, &L.ctrl->ticket[0], L.ctrl);
 }
 
 template void launch_tstage<double>(const Launch &, const Geom &, const double *, const double *, double *, int);
 template void launch_tstage<float>(const Launch &, const Geom &, const float *, const float *, float *, int);
 template void launch_wstage<double>(const Launch &, const Geom &, const double *, double *, const double *, double *, int, int);
 template void launch_wstage<float>(const Launch &, const Geom &, const float *, float *, const float *, double *, int, int);
-template void launch_mgs<double>(const Launch &, int64_t, double *, const double *, const double *, const double *, double *, int, int);
-template void launch_mgs<float>(const Launch &, int64_t, float *, const float *, const float *, const double *, double *, int, int);
+template void launch_mgs<double>(const Launch &, int64_t, double *, const double *, const double *, double *, double *, int, int, int);
+template void launch_mgs<float>(const Launch &, int64_t, float *, const float *, const float *, double *, double *, int, int, int);
 
 void launch_combine32(const Launch &L, int64_t N, const double *y0, const float *v0,
                       const float *V, int64_t ldv, float *d, double *ynext) {

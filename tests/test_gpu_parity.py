@@ -283,3 +283,40 @@ def test_full_size_first_steps(ch, oracle, c1):
         yl, pl, ll, _ = oracle.lim_step(og, y, wl["tau0"])
         assert p == pl
         assert rel(host(yn), yl) < 1e-12
+
+
+@pytest.mark.parametrize("env", [{"CH_NO_FUSED_ARNOLDI": "1"}, {"CH_NO_GRAPHS": "1"},
+                                 {"CH_NO_FUSED_ARNOLDI": "1", "CH_NO_GRAPHS": "1"}])
+@pytest.mark.parametrize("dim,n,tau", [(2, (64, 64), 1e-6), (3, (10, 9, 11), 3e-5)])
+def test_launch_variants_match_oracle(ch, oracle, monkeypatch, env, dim, n, tau):
+    """Arnoldi iterations as separate kernels, and without CUDA graphs (both read when a grid
+    is created), give the same Krylov run as the oracle."""
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    eps = 0.05
+    y = inputs.initial_state(n, 6, -0.05, 0.05)
+    with ch.Grid(dim, n, eps, mmax_capacity=30) as G:
+        yn = torch.empty(G.N, dtype=torch.float64, device="cuda")
+        tu, st = ch.ch_phi_krylov(G.h, dev(y), tau, 1e-8, 30, 0, yn)
+    rc, yo, to, jo, sto = oracle.ee_step(oracle.Grid(dim, n, eps), y, tau, tol_phi_fixed=1e-8,
+                                         mmax=30, linear_restart=False)
+    assert rc == 0
+    assert tu == pytest.approx(to, rel=1e-12, abs=0)
+    assert st["matvecs"] == sto["matvecs"]
+    assert rel(host(yn), yo) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_kernel_bench_classes(ch, precision):
+    """Every kernel class the micro-benchmark supports runs and reports its work."""
+    prec = ch.CH_FP64 if precision == "fp64" else ch.CH_MIXED
+    n = (256, 256)
+    with ch.Grid(2, n, 0.02, prec, mmax_capacity=30) as G:
+        y = dev(inputs.initial_state(n, 3))
+        ch.ch_integrate(G.h, ch.make_params("ee2", True, 1e-6, 1e-7, 1e-6, 30), y)
+        classes = ["arnoldi", "tstage", "wstage", "mgs"]
+        if precision == "fp64":
+            classes += ["resid1", "lim2", "rhs1", "rhs2"]
+        for cls in classes:
+            kb = ch.ch_bench_kernel(G.h, cls, 5)
+            assert kb["avg_us"] > 0 and kb["bytes"] > 0 and kb["flops"] > 0, cls
