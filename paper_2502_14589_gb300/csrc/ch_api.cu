@@ -671,6 +671,7 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[1], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = (cudaError_t)ch::phi_setup();
+    if (e == cudaSuccess) e = (cudaError_t)ch::arnoldi_setup();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cleanup_fail(CH_ECUDA, "grid set-up", e);
     g->L.partials = g->partials;

@@ -219,6 +219,7 @@ void launch_arnoldi(const Launch &L, int blocks, const Geom &g, VT *slot0, VT *V
                     const VT *D, VT *t, double *H, int ldh, int j);
 template <typename VT>
 int arnoldi_blocks(int dim, int64_t N);
+int arnoldi_setup();   // cudaError_t of setting the kernels' shared-memory limits
 void launch_combine32(const Launch &L, int64_t N, const double *y0, const float *v0,
                       const float *V, int64_t ldv, float *d, double *ynext);
 void launch_to32(const Launch &L, int64_t N, const double *x, float *y);

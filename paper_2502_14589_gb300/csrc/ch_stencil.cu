@@ -238,6 +238,12 @@ k_mgs(int64_t N, VT *__restrict__ w, const VT *__restrict__ vk, const VT *__rest
 // block adds the per-block partials in block order itself (the same value in every block,
 // no serialised tail); partial buffers alternate between rounds, so a fast block never
 // overwrites sums a slow block is still reading.
+//
+// FP64 on GB300 is slow per instruction as well as in throughput: a warp-wide FP64 add
+// holds its SM sub-partition for 64 cycles, and 32 warps issuing one FP64 instruction each
+// cost ~600 cycles.  Scalar work between passes (h, the next coefficient) is therefore done
+// by one thread and broadcast through shared memory, and the reduction trees use as few
+// dependent FP64 adds as the fixed summation order allows.
 // ---------------------------------------------------------------------------------------
 constexpr int kArnThreads = 1024;
 constexpr long long kBarrierSpinLimit = 1ll << 24;     // ~1 s of short sleeps
@@ -247,34 +253,47 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-
-// Grid barrier on a monotonic arrival counter.  The counter starts at 0 and every launch
-// adds the grid size once per barrier, so it is a multiple of the grid size between
-// launches and arrival number `old` belongs to the round ending at (old / G + 1) G.  One
-// atomic per block; waiting blocks poll with acquire loads (no read-modify-write traffic on
-// the line the arrivals use).  The wait is bounded: on timeout the block records CH_ETIMEOUT
-// and goes on, so the kernel always ends and the host reports the failure (and clears the
-// counter).
-__device__ __forceinline__ void grid_barrier(unsigned long long *bar, int *status) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned long long G = gridDim.x;
-        __threadfence();
-        const unsigned long long old = atomicAdd(bar, 1ull);
-        const unsigned long long target = (old / G + 1ull) * G;
-        long long spins = 0;
-        while (ld_acquire(bar) < target) {
-            if (++spins > kBarrierSpinLimit) { *status = CH_ETIMEOUT; break; }
-            __nanosleep(32);
-        }
-    }
-    __syncthreads();
+__device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Sum of one value per thread of a kArnThreads block, valid in thread 0.  FP64 adds issue
-// at 2 lanes/clk/SM, so the tree is spread over four warps (one per SM sub-partition), each
-// adding 256 values from shared memory and finishing with a shuffle tree; thread 0 adds the
-// four in order.  sh holds kArnThreads + 8 doubles.
+// Grid barrier on a monotonic arrival counter.  The counter starts at 0 and every launch
+// adds the grid size G once per barrier, so it is a multiple of G between launches.  A block
+// reads it once at kernel start: fewer than G arrivals can precede that read (nobody passes
+// the first barrier without this block), so rounding down to a multiple of G gives the
+// launch's base and round r ends when the counter reaches base + (r + 1) G.  Arrival is a
+// fire-and-forget release reduction; waiters poll with acquire loads.  Every wait is
+// bounded: on timeout the block records CH_ETIMEOUT and goes on, so the kernel always ends
+// and the host reports the failure (and clears the counter).
+struct GridBarrier {
+    unsigned long long *bar;
+    int *status;
+    unsigned long long next;   // counter value that ends the next round (thread 0)
+    __device__ __forceinline__ GridBarrier(unsigned long long *b, int *st) : bar(b), status(st), next(0) {
+        if (threadIdx.x == 0) {
+            const unsigned long long G = gridDim.x;
+            next = ld_acquire(bar) / G * G + G;
+        }
+    }
+    __device__ __forceinline__ void sync() {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            red_release_add(bar, 1ull);
+            long long spins = 0;
+            while (ld_acquire(bar) < next) {
+                if (++spins > kBarrierSpinLimit) { *status = CH_ETIMEOUT; break; }
+                __nanosleep(32);
+            }
+            next += gridDim.x;
+        }
+        __syncthreads();
+    }
+};
+
+// Sum of one value per thread of a kArnThreads block, valid in thread 0 only: four warps
+// (one per SM sub-partition) each add 256 values from shared memory and finish with a
+// shuffle tree; thread 0 adds the four in order.  sh holds kArnThreads + 8 doubles.
 __device__ __forceinline__ double arn_block_sum(double v, double *sh) {
     sh[threadIdx.x] = v;
     __syncthreads();
@@ -288,21 +307,53 @@ __device__ __forceinline__ double arn_block_sum(double v, double *sh) {
         if (lane == 0) sh[kArnThreads + wid] = a;
     }
     __syncthreads();
-    return ((sh[kArnThreads] + sh[kArnThreads + 1]) + sh[kArnThreads + 2]) + sh[kArnThreads + 3];
+    double s = 0.0;
+    if (threadIdx.x == 0) s = ((sh[kArnThreads] + sh[kArnThreads + 1]) + sh[kArnThreads + 2]) + sh[kArnThreads + 3];
+    return s;
 }
 
-// Sum of the per-block partials in block order by one warp; every thread of every block
-// gets the same value.
-__device__ __forceinline__ double arn_grid_sum(const double *part, double *sh) {
-    if (threadIdx.x < 32) {
-        double a = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) a += __ldcg(&part[b]);
+// Sum of the per-block partials in block order by warp 0 (a strided pass, then a shuffle
+// tree); the value is valid in thread 0 only and identical in every block.  Call from warp 0.
+__device__ __forceinline__ double arn_grid_sum_w0(const double *part) {
+    double a = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) a += __ldcg(&part[b]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (threadIdx.x == 0) sh[kArnThreads + 4] = a;
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// Scalars shared by the block between passes.
+template <typename VT>
+struct ArnShared {
+    double h;      // h_{k,j} of the coming pass
+    VT c;          // its coefficient h_{k,j} gam_{k-1} in the basis precision
+};
+
+// End of round k + 1 (after the barrier): sum the partials, and in thread 0
+//   k < j:  h_{k+1,j} = gam_k sum (row k of H), next coefficient h_{k+1,j} gam_k;
+//   k = j:  h_{j+1,j} = sqrt(sum) (Fig. 2 line 9), gam_j = 1 / h_{j+1,j};
+// k = 0 is the w-stage round: h_{1j} = gam_0 sum.  Block 0 writes H and the control block.
+template <typename VT>
+__device__ __forceinline__ void arn_finish_round(const double *part, int k, int j, double *H, int ldh,
+                                                 Ctrl *ctrl, ArnShared<VT> *sc) {
+    if (threadIdx.x < 32) {
+        const double sum = arn_grid_sum_w0(part);
+        if (threadIdx.x == 0) {
+            if (k < j) {
+                const double g = ctrl->gam[k];
+                const double h = g * sum;
+                sc->h = h;
+                sc->c = (VT)(h * g);
+                if (blockIdx.x == 0) H[k * ldh + (j - 1)] = h;
+            } else if (blockIdx.x == 0) {
+                const double hn = sqrt(sum);
+                ctrl->hnext2 = sum;
+                H[j * ldh + (j - 1)] = hn;
+                ctrl->gam[j] = 1.0 / hn;
+            }
+        }
     }
     __syncthreads();
-    return sh[kArnThreads + 4];
 }
 
 template <int DIM, typename VT>
@@ -311,8 +362,9 @@ k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const
           VT *__restrict__ t, double *H, int ldh, int j, double *partials, Ctrl *ctrl) {
     if (!ctrl->active) return;                  // same value in every block
     __shared__ double sh[kArnThreads + 8];
+    __shared__ ArnShared<VT> sc;
     auto W = [&](int c) -> VT * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * ldv; };
-    unsigned long long *bar = &ctrl->bar;
+    GridBarrier gb(&ctrl->bar, &ctrl->status);
     const unsigned N = (unsigned)g.N;
     const unsigned G = gridDim.x;
     const VT *x = W(j);
@@ -331,7 +383,7 @@ k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const
             t[i] = acc;
         })
     }
-    grid_barrier(bar, &ctrl->status);
+    gb.sync();
     // ---- stage 2: w = gam_j (sigma t - sum_a s_a (t_{+a} + t_{-a})), partial w . W_1
     {
         const double gam = ctrl->gam[j - 1];
@@ -351,13 +403,12 @@ k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const
         const double bsum = arn_block_sum(acc.value(), sh);
         if (threadIdx.x == 0) partials[G + blockIdx.x] = bsum;
     }
-    grid_barrier(bar, &ctrl->status);
-    double h = ctrl->gam[0] * arn_grid_sum(partials + G, sh);     // h_{1j}
-    if (blockIdx.x == 0 && threadIdx.x == 0) H[0 * ldh + (j - 1)] = h;
+    gb.sync();
+    arn_finish_round<VT>(partials + G, 0, j, H, ldh, ctrl, &sc);     // h_{1j}
     // ---- modified Gram-Schmidt passes k = 1..j (lines 5-8) and the norm of line 9
     for (int k = 1; k <= j; ++k) {
         const bool last = (k == j);
-        const VT c = (VT)(h * ctrl->gam[k - 1]);
+        const VT c = sc.c;
         const VT *vk = W(k), *vk1 = last ? W(k) : W(k + 1);
         double *part = partials + (size_t)((k + 1) & 1) * G;       // round k + 1
         DotAcc<VT> acc;
@@ -368,17 +419,139 @@ k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const
         })
         const double bsum = arn_block_sum(acc.value(), sh);
         if (threadIdx.x == 0) part[blockIdx.x] = bsum;
-        grid_barrier(bar, &ctrl->status);
-        const double sum = arn_grid_sum(part, sh);
+        gb.sync();
+        arn_finish_round<VT>(part, k, j, H, ldh, ctrl, &sc);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Shared-memory resident form of the same iteration for grids of at most R elements per
+// thread (element r of a thread is i0 + r S, S = threads in the grid: the order of
+// GRID_LOOP, so every sum and result is bit-identical to k_arnoldi).  Three buffers of
+// R x 1024 values, in slots private to each thread: w from the w-stage to the last pass
+// (stored as W_{j+1} there) and the two basis columns a pass needs.  Pass k updates with
+// v_k, dots with v_{k+1}, then starts an asynchronous copy (cp.async) of v_{k+2} into the
+// slots v_k has just left, so that load runs during the block reduction and the grid
+// barrier instead of on the critical path of the next pass; v_1 and v_2 are requested at
+// kernel start.  The passes then read only shared memory.
+// ---------------------------------------------------------------------------------------
+template <typename VT>
+__device__ __forceinline__ void cp_async_elem(VT *dst, const VT *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(VT) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Copy this thread's elements of column v into its slots of buffer b (zeros past N).
+template <typename VT>
+__device__ __forceinline__ void prefetch_col(VT *b, const VT *v, unsigned i0, unsigned S,
+                                             unsigned N, int R) {
+#pragma unroll 4
+    for (int r = 0; r < R; ++r) {
+        const unsigned i = i0 + (unsigned)r * S;
+        cp_async_elem(b + r * kArnThreads + threadIdx.x, v + (i < N ? i : 0u), i < N);
+    }
+}
+
+constexpr int kArnResMaxBytes = 3 * 8 * kArnThreads * 8;   // 3 buffers of 8 FP64 per thread
+
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kArnThreads, 1)
+k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
+              const VT *__restrict__ D, VT *__restrict__ t, double *H, int ldh, int j,
+              double *partials, Ctrl *ctrl, int R) {
+    if (!ctrl->active) return;                  // same value in every block
+    __shared__ double sh[kArnThreads + 8];
+    __shared__ ArnShared<VT> sc;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    VT *bufW = reinterpret_cast<VT *>(dyn), *bufA = bufW + R * kArnThreads,
+       *bufB = bufA + R * kArnThreads;
+    auto W = [&](int c) -> VT * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * ldv; };
+    GridBarrier gb(&ctrl->bar, &ctrl->status);
+    const unsigned N = (unsigned)g.N;
+    const unsigned G = gridDim.x, S = G * kArnThreads;
+    const unsigned i0 = blockIdx.x * kArnThreads + threadIdx.x;
+    const int me = threadIdx.x;
+    prefetch_col<VT>(bufA, W(1), i0, S, N, R);                   // v_1
+    if (j >= 2) prefetch_col<VT>(bufB, W(2), i0, S, N, R);       // v_2
+    // ---- stage 1: t = D (.) x - sum_a kap_a (x_{+a} + x_{-a})
+    {
+        const VT *x = W(j);
+        const VT k0 = (VT)g.kap[0], k1 = (VT)g.kap[1], k2 = (VT)g.kap[2];
+        GRID_LOOP2(N, {
+            VT ps[3];
+            pair_sums<DIM>(g, x, i, ps);
+            VT acc = D[i] * x[i];
+            acc = fma(-k0, ps[0], acc);
+            acc = fma(-k1, ps[1], acc);
+            if (DIM == 3) acc = fma(-k2, ps[2], acc);
+            t[i] = acc;
+        })
+    }
+    gb.sync();
+    // ---- stage 2: w = gam_j (sigma t - sum_a s_a (t_{+a} + t_{-a})), partial w . W_1
+    {
+        const double gam = ctrl->gam[j - 1];
+        const VT c0 = (VT)(gam * g.sigma), c1 = (VT)(gam * g.s[0]), c2 = (VT)(gam * g.s[1]),
+                 c3 = (VT)(gam * g.s[2]);
+        cp_async_wait_all();
+        DotAcc<VT> acc;
+        int slot = me;
+        GRID_LOOP2(N, {
+            VT ps[3];
+            pair_sums<DIM>(g, t, i, ps);
+            VT q = c0 * t[i];
+            q = fma(-c1, ps[0], q);
+            q = fma(-c2, ps[1], q);
+            if (DIM == 3) q = fma(-c3, ps[2], q);
+            bufW[slot] = q;
+            acc.add(q, bufA[slot]);
+            slot += kArnThreads;                // elements of this thread come in order
+        })
+        const double bsum = arn_block_sum(acc.value(), sh);
+        if (threadIdx.x == 0) partials[G + blockIdx.x] = bsum;
+    }
+    gb.sync();
+    arn_finish_round<VT>(partials + G, 0, j, H, ldh, ctrl, &sc);     // h_{1j}
+    VT *out = W(j + 1);
+    // elements of this thread that exist (the rest of its slots hold zeros)
+    const int Rn = i0 < N ? (int)min((unsigned)R, (N - i0 + S - 1) / S) : 0;
+    // ---- modified Gram-Schmidt passes k = 1..j (lines 5-8) and the norm of line 9;
+    //      odd passes update with buffer A and dot with B, even passes the other way round
+    for (int k = 1; k <= j; ++k) {
+        const bool last = (k == j);
+        const VT c = sc.c;
+        VT *U = (k & 1) ? bufA : bufB;
+        const VT *Dt = (k & 1) ? bufB : bufA;
+        const VT *pre = (k + 2 <= j) ? W(k + 2) : nullptr;
+        double *part = partials + (size_t)((k + 1) & 1) * G;       // round k + 1
+        cp_async_wait_all();                                       // v_{k+1} has landed
+        DotAcc<VT> acc;
         if (!last) {
-            h = ctrl->gam[k] * sum;                               // h_{k+1,j}
-            if (blockIdx.x == 0 && threadIdx.x == 0) H[k * ldh + (j - 1)] = h;
-        } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-            const double hn = sqrt(sum);                          // h_{j+1,j}
-            ctrl->hnext2 = sum;
-            H[j * ldh + (j - 1)] = hn;
-            ctrl->gam[j] = 1.0 / hn;
+#pragma unroll 4
+            for (int r = 0; r < Rn; ++r) {
+                const int slot = r * kArnThreads + me;
+                const VT x = fma(-c, U[slot], bufW[slot]);
+                bufW[slot] = x;
+                acc.add(x, Dt[slot]);
+                if (pre) cp_async_elem(U + slot, pre + i0 + (unsigned)r * S, true);  // v_{k+2}
+            }
+        } else {
+#pragma unroll 4
+            for (int r = 0; r < Rn; ++r) {
+                const int slot = r * kArnThreads + me;
+                const VT x = fma(-c, U[slot], bufW[slot]);
+                out[i0 + (unsigned)r * S] = x;
+                acc.add(x, x);
+            }
         }
+        const double bsum = arn_block_sum(acc.value(), sh);
+        if (threadIdx.x == 0) part[blockIdx.x] = bsum;
+        gb.sync();
+        arn_finish_round<VT>(part, k, j, H, ldh, ctrl, &sc);
     }
 }
 
@@ -411,10 +584,32 @@ void launch_arnoldi(const Launch &L, int blocks, const Geom &g, VT *slot0, VT *V
     cfg.numAttrs = 1;
     Ctrl *ctrl = L.ctrl;
     double *partials = L.partials;
+    const int64_t per_thread = (g.N + (int64_t)blocks * kArnThreads - 1) / ((int64_t)blocks * kArnThreads);
+    if (per_thread * 3 * kArnThreads * (int64_t)sizeof(VT) <= kArnResMaxBytes) {
+        const int R = (int)per_thread;
+        cfg.dynamicSmemBytes = (size_t)3 * R * kArnThreads * sizeof(VT);
+        if (g.dim == 3)
+            cudaLaunchKernelEx(&cfg, k_arnoldi_res<3, VT>, g, slot0, V, ldv, D, t, H, ldh, j, partials, ctrl, R);
+        else
+            cudaLaunchKernelEx(&cfg, k_arnoldi_res<2, VT>, g, slot0, V, ldv, D, t, H, ldh, j, partials, ctrl, R);
+        return;
+    }
     if (g.dim == 3)
         cudaLaunchKernelEx(&cfg, k_arnoldi<3, VT>, g, slot0, V, ldv, D, t, H, ldh, j, partials, ctrl);
     else
         cudaLaunchKernelEx(&cfg, k_arnoldi<2, VT>, g, slot0, V, ldv, D, t, H, ldh, j, partials, ctrl);
+}
+
+// Allow the resident kernels their dynamic shared memory (a function attribute, not a stream
+// operation: set at grid creation, outside any graph capture).
+int arnoldi_setup() {
+    const void *fns[] = {(const void *)k_arnoldi_res<2, double>, (const void *)k_arnoldi_res<3, double>,
+                         (const void *)k_arnoldi_res<2, float>, (const void *)k_arnoldi_res<3, float>};
+    for (const void *f : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kArnResMaxBytes);
+        if (e != cudaSuccess) return (int)e;
+    }
+    return 0;
 }
 template void launch_arnoldi<double>(const Launch &, int, const Geom &, double *, double *, int64_t,
                                      const double *, double *, double *, int, int);

@@ -320,3 +320,23 @@ def test_kernel_bench_classes(ch, precision):
         for cls in classes:
             kb = ch.ch_bench_kernel(G.h, cls, 5)
             assert kb["avg_us"] > 0 and kb["bytes"] > 0 and kb["flops"] > 0, cls
+
+
+@pytest.mark.parametrize("dim,n,tau", [
+    (2, (1100, 1100), 2e-8),      # 8 elements per thread: largest resident FP64 iteration
+    (3, (112, 112, 112), 1e-7),   # beyond it: the streaming iteration kernel
+])
+def test_arnoldi_kernel_forms_at_size(ch, oracle, dim, n, tau):
+    """The resident and the streaming form of the fused Arnoldi iteration against the oracle
+    on grids of more than a million points (one Krylov run of Fig. 2 with Eq. phi_stop)."""
+    eps = 0.02
+    y = inputs.initial_state(n, 9, -0.05, 0.05)
+    with ch.Grid(dim, n, eps, mmax_capacity=30) as G:
+        yn = torch.empty(G.N, dtype=torch.float64, device="cuda")
+        tu, st = ch.ch_phi_krylov(G.h, dev(y), tau, 1e-8, 30, 0, yn)
+    rc, yo, to, jo, sto = oracle.ee_step(oracle.Grid(dim, n, eps), y, tau, tol_phi_fixed=1e-8,
+                                         mmax=30, linear_restart=False)
+    assert rc == 0
+    assert tu == pytest.approx(to, rel=1e-12, abs=0)
+    assert st["matvecs"] == sto["matvecs"]
+    assert rel(host(yn), yo) < 1e-12
