@@ -42,7 +42,7 @@ except Exception:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c1_2d1024_adaptive")
@@ -271,6 +271,8 @@ def main():
     G = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_FP64, wl["mmax"], stream)
     prm = {s: ch.make_params(s, True, wl["T"], wl["tau0"], wl["tol"], wl["mmax"]) for s in ("ee2", "lim")}
 
+    y_ee2 = torch.empty_like(y0)              # EE2 solution at T of the last step
+
     def one_step(yin_dev, record=None):
         stats = {}
         for s in ("ee2", "lim"):
@@ -279,6 +281,8 @@ def main():
             e0.record(stream)
             stats[s] = ch.ch_integrate(G.h, prm[s], y)
             e1.record(stream)
+            if s == "ee2":
+                y_ee2.copy_(y)
             if record is not None:
                 record[s].append((e0, e1, stats[s]))
         return stats
@@ -334,13 +338,12 @@ def main():
     # ---- mixed precision on the same instance: time to T and error at T against FP64 ----
     mixed = None
     if not args.no_mixed:
-        y.copy_(y0)
-        ch.ch_integrate(G.h, prm["ee2"], y)
-        y_fp64 = y.clone()
+        y_fp64 = y_ee2.clone()                            # FP64 EE2 at T from the timed step
         Gm = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_MIXED, wl["mmax"], stream)
         ym = torch.empty_like(y0)
         ym.copy_(y0)
-        ch.ch_integrate(Gm.h, prm["ee2"], ym)            # warm-up (graph capture)
+        pw = ch.make_params("ee2", True, wl["T"] / 10, wl["tau0"], wl["tol"], wl["mmax"])
+        ch.ch_integrate(Gm.h, pw, ym)                     # warm-up (graph capture)
         ym.copy_(y0)
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
@@ -376,9 +379,8 @@ def main():
         e2e = {"value": e2e_ops / (e2e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": 2 * N * 8}
 
-    # ---- roofline: every streaming kernel class timed on the workload grid ---------------
-    # (CUDA events on the grid's stream around a graph of back-to-back launches); the
-    # dominant class is the one with the largest launches x mean duration in the timed region
+    # ---- per-class kernel table: each class timed on the workload grid with CUDA events on
+    # the grid's stream around a graph of 200 back-to-back launches (Arnoldi iteration at j = 10)
     kernels = {}
     classes = ("arnoldi", "tstage", "wstage", "mgs", "resid1", "lim2", "rhs1", "rhs2")
     for cls in (() if args.no_roofline else classes):
@@ -391,25 +393,47 @@ def main():
                         "gbs": kb["bytes"] / dur / 1e9, "tflops": kb["flops"] / dur / 1e12,
                         "fp64_issue_frac": kb["fp64_instr"] / dur / FP64_ISSUE_PEAK,
                         "bytes": kb["bytes"], "flops": kb["flops"], "fp64_instr": kb["fp64_instr"]}
-    roof = None
+    # ---- roofline of the dominant kernel, measured live: every launch of its class timed
+    # with CUDA events on the grid's stream over the first twentieth of the workload's run
+    # (t in [0, T/20], the same kernels and Krylov dimensions as the timed region; CUDA
+    # graphs are off while launches are timed), with the algorithmic work of each launch
+    # summed by the library (flops and bytes per point times the points of the launch)
+    roof, live = None, {}
     if kernels:
+        for cls, scheme in (("arnoldi", "ee2"), ("lim2", "lim")):
+            if cls not in kernels:
+                continue
+            y.copy_(y0)
+            ch.ch_timing_start(G.h, cls)
+            seg = ch.make_params(scheme, True, wl["T"] / 20, wl["tau0"], wl["tol"], wl["mmax"])
+            ch.ch_integrate(G.h, seg, y)
+            ms, nt, _ = ch.ch_timing_read(G.h)
+            fl, by = ch.ch_timing_work(G.h)
+            ch.ch_timing_start(G.h, None)
+            if nt > 0 and ms > 0:
+                live[cls] = {"launches": nt, "avg_us": 1e3 * ms / nt, "tflops": fl / (ms * 1e-3) / 1e12,
+                             "gbs": by / (ms * 1e-3) / 1e9, "flops_per_launch": fl / nt,
+                             "bytes_per_launch": by / nt}
         dom = max(kernels, key=lambda c: kernels[c]["est_share_s"])
-        kd = kernels[dom]
-        roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": kd["tflops"],
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kd["tflops"] / FP64_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                "fp64_issue_frac": kd["fp64_issue_frac"], "avg_launch_us": kd["avg_us"],
-                "algorithmic_bytes_per_launch": kd["bytes"], "achieved_gbs": kd["gbs"],
-                "hbm_frac_of_measured": kd["gbs"] / HBM_GBS}
+        if dom in live:
+            kl = live[dom]
+            roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": kl["tflops"],
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kl["tflops"] / FP64_PEAK_TFLOPS,
+                    "traffic": None,
+                    "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 pipe)",
+                    "measured": f"{kl['launches']} launches timed live over t in [0, T/20]",
+                    "avg_launch_us": kl["avg_us"], "algorithmic_flops_per_launch": kl["flops_per_launch"],
+                    "algorithmic_bytes_per_launch": kl["bytes_per_launch"], "achieved_gbs": kl["gbs"],
+                    "hbm_frac_of_measured": kl["gbs"] / HBM_GBS}
 
     # ---- CPU baseline (oracle on a bounded sample, rank 0 only, N = 1) -----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle
         oracle.build()
-        c_ops, c_s = oracle_sample(wl, 0, 4)
+        c_ops, c_s = oracle_sample(wl, 0, 12)
         cpu = {"value": c_ops / c_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first 4 adaptive EE2 steps + first 4 adaptive LIM steps of the same "
+               "sample": "first 12 adaptive EE2 steps + first 12 adaptive LIM steps of the same "
                          f"workload (seed 0), {c_s:.1f} s single-threaded on the host"}
 
     if rank == 0:
@@ -421,7 +445,7 @@ def main():
                        "grid_points": N, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed (256 MiB write) before every timed step"},
             "time_to_T": ttt, "e2e": e2e, "gpu_launches": launches, "launches_by_kernel": counts,
-            "mixed": mixed, "roofline": roof, "kernels": kernels, "hbm_peak_gbs": HBM_GBS, "cpu_baseline": cpu,
+            "mixed": mixed, "roofline": roof, "kernels": kernels, "kernels_live": live, "hbm_peak_gbs": HBM_GBS, "cpu_baseline": cpu,
             "clocks": clk,
         }
         print(json.dumps(out), flush=True)

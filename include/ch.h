@@ -197,6 +197,14 @@ ch_status ch_timing_start(ch_grid *g, int kernel_class);
 ch_status ch_timing_read(ch_grid *g, double *total_ms, int64_t *timed_launches,
                          int64_t *counts);
 
+/* Algorithmic work of the launches timed since ch_timing_start: floating-point operations
+ * (an FMA counts 2) and the bytes the method must move, as each launch computes them from
+ * its sizes.  Reported by the classes CH_K_ARNOLDI (Arnoldi iteration j on N points:
+ * (4 + 6d + 4j) N flops, (5 + j) N values moved), CH_K_RESID1 ((2 + 3d) N flops, 32 N
+ * bytes) and CH_K_LIM2 ((5 + 3d) N flops, 32 N bytes); 0 for the others.  Does not
+ * synchronise; read it after ch_timing_read.                                            */
+ch_status ch_timing_work(ch_grid *g, double *flops, double *bytes);
+
 /* Time one kernel class in isolation on this grid's current workspace: R back-to-back
  * launches captured in a CUDA graph, CUDA events on the grid's stream around the graph.
  * Returns the mean duration of one launch and its algorithmic traffic and arithmetic per

@@ -65,6 +65,7 @@ _SIGS = {
     "ch_energy_mass": [_P, _P, _DP, _DP],
     "ch_timing_start": [_P, C.c_int],
     "ch_timing_read": [_P, _DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+    "ch_timing_work": [_P, _DP, _DP],
     "ch_bench_kernel": [_P, C.c_int, C.c_int, _DP, _DP, _DP, _DP],
     "ch_create_batch": [C.c_int, C.c_int, C.POINTER(C.c_int64), _DP, C.c_int, C.c_int, _P, C.POINTER(_P)],
     "ch_destroy_batch": [_P],
@@ -248,6 +249,12 @@ def ch_timing_read(h):
     ms = C.c_double(); n = C.c_int64(); counts = (C.c_int64 * len(KERNEL_CLASSES))()
     _check(load().ch_timing_read(h, C.byref(ms), C.byref(n), counts))
     return ms.value, n.value, {k: counts[i] for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def ch_timing_work(h):
+    f, b = C.c_double(), C.c_double()
+    _check(load().ch_timing_work(h, C.byref(f), C.byref(b)))
+    return f.value, b.value
 
 
 class Grid:

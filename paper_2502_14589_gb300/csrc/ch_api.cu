@@ -456,7 +456,15 @@ ch_status ch_timing_start(ch_grid *g, int kernel_class) {
     g->timing.used = 0;
     g->timing.total_ms = 0.0;
     g->timing.timed = 0;
+    g->timing.flops = g->timing.bytes = 0.0;
     for (auto &c : g->timing.counts) c = 0;
+    return CH_OK;
+}
+
+ch_status ch_timing_work(ch_grid *g, double *flops, double *bytes) {
+    if (!g) return fail(CH_EINVAL, "null grid");
+    if (flops) *flops = g->timing.flops;
+    if (bytes) *bytes = g->timing.bytes;
     return CH_OK;
 }
 
@@ -519,7 +527,7 @@ ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us
             const int j = std::min(10, g->mmax_cap);
             if (mixed) ch::launch_arnoldi<float>(Lc, g->arn_blocks, g->g, g->Wf[0], g->Vf, g->ldv, g->Df, g->tf, g->H, g->mmax_cap, j);
             else ch::launch_arnoldi<double>(Lc, g->arn_blocks, g->g, g->F[0], g->V, g->ldv, g->D, g->t, g->H, g->mmax_cap, j);
-            bytes = (6 + 4.0 * j) * vb * N;
+            bytes = (5.0 + j) * vb * N;
             flops = ((1 + 3.0 * d) + (3 + 3.0 * d) + 4.0 * j) * N;
             instr = mixed ? 0 : ((1 + 2.0 * d) + (2 + 2.0 * d) + 2.0 * j) * N;
             break;

@@ -162,6 +162,7 @@ struct Timing {
     double total_ms = 0.0;
     int64_t timed = 0;
     int64_t counts[CH_K_COUNT] = {0};
+    double flops = 0.0, bytes = 0.0;    // algorithmic work of the timed launches
     void harvest();                     // defined in ch_api.cu
 };
 
@@ -191,6 +192,13 @@ struct LaunchScope {
                 timed = true;
             }
         }
+    }
+    // Algorithmic work of this launch (floating-point operations, an FMA counting 2, and the
+    // bytes the method must move), accumulated when the launch is timed.
+    void work(double flops, double bytes) const {
+        if (!timed) return;
+        L.timing->flops += flops;
+        L.timing->bytes += bytes;
     }
     ~LaunchScope() {
         if (!timed) return;

@@ -275,48 +275,63 @@ struct GridBarrier {
             next = ld_acquire(bar) / G * G + G;
         }
     }
+    // Thread 0 arrives and waits.  The release reduction orders the block's earlier writes
+    // (made visible to thread 0 by a preceding __syncthreads) before the arrival.
+    __device__ __forceinline__ void arrive_wait_t0() {
+        red_release_add(bar, 1ull);
+        long long spins = 0;
+        while (ld_acquire(bar) < next) {
+            if (++spins > kBarrierSpinLimit) { *status = CH_ETIMEOUT; break; }
+            __nanosleep(32);
+        }
+        next += gridDim.x;
+    }
+    // Whole-block barrier across the grid.
     __device__ __forceinline__ void sync() {
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            red_release_add(bar, 1ull);
-            long long spins = 0;
-            while (ld_acquire(bar) < next) {
-                if (++spins > kBarrierSpinLimit) { *status = CH_ETIMEOUT; break; }
-                __nanosleep(32);
-            }
-            next += gridDim.x;
-        }
+        if (threadIdx.x == 0) arrive_wait_t0();
         __syncthreads();
+    }
+    // Warp-0 barrier across the grid, for rounds where only thread 0 has written data other
+    // blocks read (its partial sum): the rest of the block need not wait on it.
+    __device__ __forceinline__ void sync_w0() {
+        if (threadIdx.x == 0) arrive_wait_t0();
+        __syncwarp();
     }
 };
 
 // Sum of one value per thread of a kArnThreads block, valid in thread 0 only: four warps
-// (one per SM sub-partition) each add 256 values from shared memory and finish with a
-// shuffle tree; thread 0 adds the four in order.  sh holds kArnThreads + 8 doubles.
+// (one per SM sub-partition) each add 256 values from shared memory (8 per lane as a
+// pairwise tree) and finish with a shuffle tree; thread 0 adds the four pairwise.  Ten
+// dependent FP64 adds in all.  sh holds kArnThreads + 8 doubles.
 __device__ __forceinline__ double arn_block_sum(double v, double *sh) {
     sh[threadIdx.x] = v;
     __syncthreads();
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (wid < 4) {
-        double a = 0.0;
-#pragma unroll
-        for (int r = 0; r < kArnThreads / 128; ++r) a += sh[wid * (kArnThreads / 4) + r * 32 + lane];
+        const double *p = sh + wid * (kArnThreads / 4) + lane;
+        double a = ((p[0] + p[32]) + (p[64] + p[96])) + ((p[128] + p[160]) + (p[192] + p[224]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
         if (lane == 0) sh[kArnThreads + wid] = a;
     }
     __syncthreads();
     double s = 0.0;
-    if (threadIdx.x == 0) s = ((sh[kArnThreads] + sh[kArnThreads + 1]) + sh[kArnThreads + 2]) + sh[kArnThreads + 3];
+    if (threadIdx.x == 0) s = (sh[kArnThreads] + sh[kArnThreads + 1]) + (sh[kArnThreads + 2] + sh[kArnThreads + 3]);
     return s;
 }
 
-// Sum of the per-block partials in block order by warp 0 (a strided pass, then a shuffle
-// tree); the value is valid in thread 0 only and identical in every block.  Call from warp 0.
+constexpr int kMaxArnBlocks = 32 * 5;   // grid of the iteration kernels: at most 5 partials per lane
+
+// Sum of the per-block partials by warp 0 (lane l adds slots l + 32 s pairwise over s, then
+// a shuffle tree); the value is valid in thread 0 only and identical in every block.  The
+// loads are issued together, so the L2 round trip is paid once.  Call from warp 0.
 __device__ __forceinline__ double arn_grid_sum_w0(const double *part) {
-    double a = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) a += __ldcg(&part[b]);
+    const unsigned G = gridDim.x, lane = threadIdx.x;
+    double v[5];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) v[s] = (lane + 32u * s < G) ? __ldcg(&part[lane + 32u * s]) : 0.0;
+    double a = ((v[0] + v[1]) + (v[2] + v[3])) + v[4];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
     return a;
@@ -329,14 +344,16 @@ struct ArnShared {
     VT c;          // its coefficient h_{k,j} gam_{k-1} in the basis precision
 };
 
-// End of round k + 1 (after the barrier): sum the partials, and in thread 0
+// End of round k + 1 (thread 0 has posted this block's partial): warp 0 waits at the grid
+// barrier and sums the partials, and in thread 0
 //   k < j:  h_{k+1,j} = gam_k sum (row k of H), next coefficient h_{k+1,j} gam_k;
 //   k = j:  h_{j+1,j} = sqrt(sum) (Fig. 2 line 9), gam_j = 1 / h_{j+1,j};
 // k = 0 is the w-stage round: h_{1j} = gam_0 sum.  Block 0 writes H and the control block.
 template <typename VT>
-__device__ __forceinline__ void arn_finish_round(const double *part, int k, int j, double *H, int ldh,
-                                                 Ctrl *ctrl, ArnShared<VT> *sc) {
+__device__ __forceinline__ void arn_finish_round(GridBarrier &gb, const double *part, int k, int j,
+                                                 double *H, int ldh, Ctrl *ctrl, ArnShared<VT> *sc) {
     if (threadIdx.x < 32) {
+        gb.sync_w0();
         const double sum = arn_grid_sum_w0(part);
         if (threadIdx.x == 0) {
             if (k < j) {
@@ -403,8 +420,7 @@ k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const
         const double bsum = arn_block_sum(acc.value(), sh);
         if (threadIdx.x == 0) partials[G + blockIdx.x] = bsum;
     }
-    gb.sync();
-    arn_finish_round<VT>(partials + G, 0, j, H, ldh, ctrl, &sc);     // h_{1j}
+    arn_finish_round<VT>(gb, partials + G, 0, j, H, ldh, ctrl, &sc);     // h_{1j}
     // ---- modified Gram-Schmidt passes k = 1..j (lines 5-8) and the norm of line 9
     for (int k = 1; k <= j; ++k) {
         const bool last = (k == j);
@@ -419,8 +435,7 @@ k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const
         })
         const double bsum = arn_block_sum(acc.value(), sh);
         if (threadIdx.x == 0) part[blockIdx.x] = bsum;
-        gb.sync();
-        arn_finish_round<VT>(part, k, j, H, ldh, ctrl, &sc);
+        arn_finish_round<VT>(gb, part, k, j, H, ldh, ctrl, &sc);
     }
 }
 
@@ -514,8 +529,7 @@ k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
         const double bsum = arn_block_sum(acc.value(), sh);
         if (threadIdx.x == 0) partials[G + blockIdx.x] = bsum;
     }
-    gb.sync();
-    arn_finish_round<VT>(partials + G, 0, j, H, ldh, ctrl, &sc);     // h_{1j}
+    arn_finish_round<VT>(gb, partials + G, 0, j, H, ldh, ctrl, &sc);     // h_{1j}
     VT *out = W(j + 1);
     // elements of this thread that exist (the rest of its slots hold zeros)
     const int Rn = i0 < N ? (int)min((unsigned)R, (N - i0 + S - 1) / S) : 0;
@@ -550,8 +564,7 @@ k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
         }
         const double bsum = arn_block_sum(acc.value(), sh);
         if (threadIdx.x == 0) part[blockIdx.x] = bsum;
-        gb.sync();
-        arn_finish_round<VT>(part, k, j, H, ldh, ctrl, &sc);
+        arn_finish_round<VT>(gb, part, k, j, H, ldh, ctrl, &sc);
     }
 }
 
@@ -563,7 +576,7 @@ int arnoldi_blocks(int dim, int64_t N) {
     if (dim == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<3, VT>, kArnThreads, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<2, VT>, kArnThreads, 0);
     const int64_t want = (N + 2 * kArnThreads - 1) / (2 * kArnThreads);
-    return (int)std::min<int64_t>(want, (int64_t)per_sm * sms);
+    return (int)std::min<int64_t>(std::min<int64_t>(want, (int64_t)per_sm * sms), kMaxArnBlocks);
 }
 template int arnoldi_blocks<double>(int, int64_t);
 template int arnoldi_blocks<float>(int, int64_t);
@@ -572,6 +585,11 @@ template <typename VT>
 void launch_arnoldi(const Launch &L, int blocks, const Geom &g, VT *slot0, VT *V, int64_t ldv,
                     const VT *D, VT *t, double *H, int ldh, int j) {
     LaunchScope scope(L, CH_K_ARNOLDI);
+    {   // stage 1: mul + d (add + fma); stage 2: the same + the dot fma; j passes of 2 fma.
+        // Bytes: x, D, t written, t read, v_1..v_j read once, W_{j+1} written.
+        const double N = (double)g.N, d = g.dim;
+        scope.work(((1.0 + 3.0 * d) + (3.0 + 3.0 * d) + 4.0 * j) * N, (5.0 + j) * sizeof(VT) * N);
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks, 1, 1);
     cfg.blockDim = dim3(kArnThreads, 1, 1);
@@ -976,7 +994,10 @@ void launch_rhs2(const Launch &L, const Geom &g, const double *mu, const double 
 
 void launch_resid1(const Launch &L, const Geom &g, const double *x, const double *D,
                    const double *G, double *t) {
-    DISPATCH_DIM(CH_K_RESID1, g, k_resid1, g, x, D, G, t);
+    LaunchScope scope(L, CH_K_RESID1);
+    scope.work((2.0 + 3.0 * g.dim) * g.N, 32.0 * g.N);      // fma + d (add + fma); x, D, G, t
+    if (g.dim == 3) k_resid1<3><<<L.blocks, kThreads, 0, L.stream>>>(g, x, D, G, t);
+    else k_resid1<2><<<L.blocks, kThreads, 0, L.stream>>>(g, x, D, G, t);
 }
 
 void launch_resid2(const Launch &L, const Geom &g, const double *t, double *out) {
@@ -985,7 +1006,10 @@ void launch_resid2(const Launch &L, const Geom &g, const double *t, double *out)
 
 void launch_lim2(const Launch &L, const Geom &g, const double *t, const double *yn,
                  const double *yprev, double *ynext, double tau_a, double tau, double alpha) {
-    DISPATCH_DIM(CH_K_LIM2, g, k_lim2, g, t, yn, yprev, ynext, tau_a, tau, alpha);
+    LaunchScope scope(L, CH_K_LIM2);
+    scope.work((5.0 + 3.0 * g.dim) * g.N, 32.0 * g.N);      // stage 2 + update; t, yn, yprev, ynext
+    if (g.dim == 3) k_lim2<3><<<L.blocks, kThreads, 0, L.stream>>>(g, t, yn, yprev, ynext, tau_a, tau, alpha);
+    else k_lim2<2><<<L.blocks, kThreads, 0, L.stream>>>(g, t, yn, yprev, ynext, tau_a, tau, alpha);
 }
 
 void launch_energy(const Launch &L, const Geom &g, const double *y) {
