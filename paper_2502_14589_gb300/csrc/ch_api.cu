@@ -288,10 +288,11 @@ static ch_status krylov_run(ch_grid *g, const double *y0, int s, double tau0,
 }
 
 // Linearisation coefficients of A_hat_n at yn (and G for residuals / LIM) in FP64; mixed
-// grids also keep an FP32 copy of D for the Krylov matvecs.
+// grids also keep J = D - eps^2 sigma in FP32 for the Krylov matvecs.
 static void prep(ch_grid *g, const double *yn, int eyre, int want_G, int want_minmax) {
     ch::launch_prep(g->L, g->g, yn, eyre, g->D, want_G ? g->G : nullptr, want_minmax);
-    if (g->precision == CH_MIXED) ch::launch_to32(g->L, g->g.N, g->D, g->Df);
+    // FP32 stages take J (+1 Eyre) = D - eps^2 sigma (the difference form of the stages)
+    if (g->precision == CH_MIXED) ch::launch_to32(g->L, g->g.N, g->D, g->Df, -g->g.eps2 * g->g.sigma);
 }
 
 static void add_record(ch_grid *g, const StepRecord &r) {

@@ -99,6 +99,23 @@ __device__ __forceinline__ void pair_sums_inst(const Inst &I, const T *__restric
     }
 }
 
+// Differences (x_l - x_{l+a}) + (x_l - x_{l-a}) along every axis of an instance (FP32 stages).
+template <int DIM, typename T>
+__device__ __forceinline__ void pair_diffs_inst(const Inst &I, const T *__restrict__ x, unsigned l,
+                                                T (&pd)[3]) {
+    const unsigned n0 = (unsigned)I.n[0], n1 = (unsigned)I.n[1];
+    const unsigned c0 = l % n0, r = l / n0, c1 = r % n1;
+    const T xl = x[l];
+    pd[0] = (xl - x[bnp(l, c0, n0, 1u)]) + (xl - x[bnm(l, c0, n0, 1u)]);
+    pd[1] = (xl - x[bnp(l, c1, n1, n0)]) + (xl - x[bnm(l, c1, n1, n0)]);
+    if (DIM == 3) {
+        const unsigned n2 = (unsigned)I.n[2], s2 = n0 * n1, c2 = r / n1;
+        pd[2] = (xl - x[bnp(l, c2, n2, s2)]) + (xl - x[bnm(l, c2, n2, s2)]);
+    } else {
+        pd[2] = T(0);
+    }
+}
+
 template <typename VT> struct BDot;
 template <> struct BDot<double> {
     double s = 0.0;
@@ -154,14 +171,15 @@ __device__ __forceinline__ void inst_sum(double (&v)[K], const Inst &I, int inst
 
 #define CHUNK_LOOP(l) for (unsigned l = ck.begin + threadIdx.x; l < (unsigned)ck.end; l += blockDim.x)
 
-// ---- per-step coefficients: D = 3y^2 - 1 + eps^2 sigma (in the basis precision) -----------
+// ---- per-step coefficients in the basis precision: FP64 D = 3y^2 - 1 + eps^2 sigma for the
+// pair-sum stages, FP32 J = 3y^2 - 1 for the difference-form stages (see kb_tstage) --------
 template <typename VT>
 __global__ void __launch_bounds__(kThreads)
 kb_prep(const Inst *insts, const Chunk *chunks, const BState *bs, const double *__restrict__ y,
         VT *__restrict__ D) {
     CHUNK_BEGIN
     if (bs[ck.inst].done) return;
-    const double dconst = -1.0 + I.eps2 * I.sigma;
+    const double dconst = sizeof(VT) == 8 ? -1.0 + I.eps2 * I.sigma : -1.0;
     CHUNK_LOOP(l) {
         const double yi = y[I.off + l];
         D[I.off + l] = (VT)fma(3.0, yi * yi, dconst);
@@ -272,13 +290,22 @@ kb_tstage(const Inst *insts, const Chunk *chunks, const Ctrl *ctrls, const VT *_
     if (!ctrls[ck.inst].active) return;
     const VT *xi = x + I.off;
     const VT k0 = (VT)I.kap[0], k1 = (VT)I.kap[1], k2 = (VT)I.kap[2];
+    // FP64: pair-sum form with D; FP32: difference form with J (no cancellation of the
+    // eps^2 sigma x term or of the smooth part of the neighbour sums in FP32 rounding)
     CHUNK_LOOP(l) {
-        VT ps[3];
-        pair_sums_inst<DIM>(I, xi, l, ps);
+        VT q[3];
         VT acc = D[I.off + l] * xi[l];
-        acc = fma(-k0, ps[0], acc);
-        acc = fma(-k1, ps[1], acc);
-        if (DIM == 3) acc = fma(-k2, ps[2], acc);
+        if constexpr (sizeof(VT) == 8) {
+            pair_sums_inst<DIM>(I, xi, l, q);
+            acc = fma(-k0, q[0], acc);
+            acc = fma(-k1, q[1], acc);
+            if (DIM == 3) acc = fma(-k2, q[2], acc);
+        } else {
+            pair_diffs_inst<DIM>(I, xi, l, q);
+            acc = fma(k0, q[0], acc);
+            acc = fma(k1, q[1], acc);
+            if (DIM == 3) acc = fma(k2, q[2], acc);
+        }
         t[I.off + l] = acc;
     }
 }
@@ -297,12 +324,20 @@ kb_wstage(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, const VT *__restr
     const VT *ti = t + I.off;
     BDot<VT> acc;
     CHUNK_LOOP(l) {
-        VT ps[3];
-        pair_sums_inst<DIM>(I, ti, l, ps);
-        VT r = c0 * ti[l];
-        r = fma(-c1, ps[0], r);
-        r = fma(-c2, ps[1], r);
-        if (DIM == 3) r = fma(-c3, ps[2], r);
+        VT q[3];
+        VT r;
+        if constexpr (sizeof(VT) == 8) {
+            pair_sums_inst<DIM>(I, ti, l, q);
+            r = c0 * ti[l];
+            r = fma(-c1, q[0], r);
+            r = fma(-c2, q[1], r);
+            if (DIM == 3) r = fma(-c3, q[2], r);
+        } else {
+            pair_diffs_inst<DIM>(I, ti, l, q);
+            r = c1 * q[0];
+            r = fma(c2, q[1], r);
+            if (DIM == 3) r = fma(c3, q[2], r);
+        }
         w[I.off + l] = r;
         acc.add(r, v1[I.off + l]);
     }

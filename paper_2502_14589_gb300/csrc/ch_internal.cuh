@@ -230,7 +230,7 @@ int arnoldi_blocks(int dim, int64_t N);
 int arnoldi_setup();   // cudaError_t of setting the kernels' shared-memory limits
 void launch_combine32(const Launch &L, int64_t N, const double *y0, const float *v0,
                       const float *V, int64_t ldv, float *d, double *ynext);
-void launch_to32(const Launch &L, int64_t N, const double *x, float *y);
+void launch_to32(const Launch &L, int64_t N, const double *x, float *y, double shift = 0.0);
 void launch_combine(const Launch &L, int64_t N, const double *y0, const double *v0,
                     const double *V, int64_t ldv, double *ynext);
 void launch_rhs1(const Launch &L, const Geom &g, const double *y, int eyre, double *mu,

@@ -41,6 +41,70 @@ __device__ __forceinline__ void pair_sums(const Geom &g, const T *__restrict__ x
     }
 }
 
+// Differences (x_i - x_{i+a}) + (x_i - x_{i-a}) along every axis (the FP32 stages).
+template <int DIM, typename T>
+__device__ __forceinline__ void pair_diffs(const Geom &g, const T *__restrict__ x, unsigned i,
+                                           T (&pd)[3]) {
+    const unsigned n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    const unsigned c0 = i % n0;
+    const unsigned r = i / n0;
+    const unsigned c1 = r % n1;
+    const T xi = x[i];
+    pd[0] = (xi - x[nb_p(i, c0, n0, 1u)]) + (xi - x[nb_m(i, c0, n0, 1u)]);
+    pd[1] = (xi - x[nb_p(i, c1, n1, n0)]) + (xi - x[nb_m(i, c1, n1, n0)]);
+    if (DIM == 3) {
+        const unsigned n2 = (unsigned)g.n[2], s2 = n0 * n1;
+        const unsigned c2 = r / n1;
+        pd[2] = (xi - x[nb_p(i, c2, n2, s2)]) + (xi - x[nb_m(i, c2, n2, s2)]);
+    } else {
+        pd[2] = T(0);
+    }
+}
+
+// The two stages of A_hat v in the basis precision, at point i.
+//   FP64: t = D x - sum_a kap_a (x_{+a} + x_{-a}),  D = J + eps^2 sigma  (fewest FP64 ops);
+//         w = c0 t - sum_a c_a (t_{+a} + t_{-a}).
+//   FP32: t = J x + sum_a kap_a ((x - x_{+a}) + (x - x_{-a})),  D holds J (+1 Eyre);
+//         w = sum_a c_a ((t - t_{+a}) + (t - t_{-a})).
+// The FP32 form is the same operator without the cancellation of the pair-sum form: there
+// the eps^2 sigma x term (about 400 x at 1024^2, eps = 0.01) and the smooth part of the
+// neighbour sums cancel in FP32 rounding, while neighbour differences of a smooth field are
+// exact (Sterbenz) and only the small second differences are rounded.
+template <int DIM, typename VT>
+__device__ __forceinline__ VT stage1_at(const Geom &g, const VT *__restrict__ x,
+                                        const VT *__restrict__ D, unsigned i, VT k0, VT k1, VT k2) {
+    VT q[3];
+    VT acc = D[i] * x[i];
+    if constexpr (sizeof(VT) == 8) {
+        pair_sums<DIM>(g, x, i, q);
+        k0 = -k0; k1 = -k1; k2 = -k2;
+    } else {
+        pair_diffs<DIM>(g, x, i, q);
+    }
+    acc = fma(k0, q[0], acc);
+    acc = fma(k1, q[1], acc);
+    if (DIM == 3) acc = fma(k2, q[2], acc);
+    return acc;
+}
+template <int DIM, typename VT>
+__device__ __forceinline__ VT stage2_at(const Geom &g, const VT *__restrict__ t, unsigned i,
+                                        VT c0, VT c1, VT c2, VT c3) {
+    VT q[3];
+    VT r;
+    if constexpr (sizeof(VT) == 8) {
+        pair_sums<DIM>(g, t, i, q);
+        r = c0 * t[i];
+        c1 = -c1; c2 = -c2; c3 = -c3;
+        r = fma(c1, q[0], r);
+    } else {
+        pair_diffs<DIM>(g, t, i, q);
+        r = c1 * q[0];
+    }
+    r = fma(c2, q[1], r);
+    if (DIM == 3) r = fma(c3, q[2], r);
+    return r;
+}
+
 // Dot-product accumulators.  FP64 vectors: plain FMA accumulation.  FP32 vectors (mixed
 // precision): every product is split exactly into p + e (e = fma(a, b, -p)) and summed with
 // a compensated two-sum in FP32 pairs, so the per-thread sum carries ~2^-44 relative error;
@@ -138,13 +202,7 @@ k_tstage(Geom g, const VT *__restrict__ x, const VT *__restrict__ D, VT *__restr
     if (guarded && !ctrl->active) return;
     const VT k0 = (VT)g.kap[0], k1 = (VT)g.kap[1], k2 = (VT)g.kap[2];
     GRID_LOOP2(g.N, {
-        VT ps[3];
-        pair_sums<DIM>(g, x, i, ps);
-        VT acc = D[i] * x[i];
-        acc = fma(-k0, ps[0], acc);
-        acc = fma(-k1, ps[1], acc);
-        if (DIM == 3) acc = fma(-k2, ps[2], acc);
-        t[i] = acc;
+        t[i] = stage1_at<DIM, VT>(g, x, D, i, k0, k1, k2);
     })
 }
 
@@ -158,12 +216,7 @@ k_wstage(Geom g, const VT *__restrict__ t, VT *__restrict__ w, const VT *__restr
              c3 = (VT)(gam * g.s[2]);
     DotAcc<VT> acc;
     GRID_LOOP2(g.N, {
-        VT ps[3];
-        pair_sums<DIM>(g, t, i, ps);
-        VT r = c0 * t[i];
-        r = fma(-c1, ps[0], r);
-        r = fma(-c2, ps[1], r);
-        if (DIM == 3) r = fma(-c3, ps[2], r);
+        const VT r = stage2_at<DIM, VT>(g, t, i, c0, c1, c2, c3);
         w[i] = r;
         if (v1) acc.add(r, v1[i]);
     })
@@ -391,13 +444,7 @@ k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const
     {
         const VT k0 = (VT)g.kap[0], k1 = (VT)g.kap[1], k2 = (VT)g.kap[2];
         GRID_LOOP2(N, {
-            VT ps[3];
-            pair_sums<DIM>(g, x, i, ps);
-            VT acc = D[i] * x[i];
-            acc = fma(-k0, ps[0], acc);
-            acc = fma(-k1, ps[1], acc);
-            if (DIM == 3) acc = fma(-k2, ps[2], acc);
-            t[i] = acc;
+            t[i] = stage1_at<DIM, VT>(g, x, D, i, k0, k1, k2);
         })
     }
     gb.sync();
@@ -408,12 +455,7 @@ k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const
                  c3 = (VT)(gam * g.s[2]);
         DotAcc<VT> acc;
         GRID_LOOP2(N, {
-            VT ps[3];
-            pair_sums<DIM>(g, t, i, ps);
-            VT r = c0 * t[i];
-            r = fma(-c1, ps[0], r);
-            r = fma(-c2, ps[1], r);
-            if (DIM == 3) r = fma(-c3, ps[2], r);
+            const VT r = stage2_at<DIM, VT>(g, t, i, c0, c1, c2, c3);
             w[i] = r;
             acc.add(r, v1[i]);
         })
@@ -497,13 +539,7 @@ k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
         const VT *x = W(j);
         const VT k0 = (VT)g.kap[0], k1 = (VT)g.kap[1], k2 = (VT)g.kap[2];
         GRID_LOOP2(N, {
-            VT ps[3];
-            pair_sums<DIM>(g, x, i, ps);
-            VT acc = D[i] * x[i];
-            acc = fma(-k0, ps[0], acc);
-            acc = fma(-k1, ps[1], acc);
-            if (DIM == 3) acc = fma(-k2, ps[2], acc);
-            t[i] = acc;
+            t[i] = stage1_at<DIM, VT>(g, x, D, i, k0, k1, k2);
         })
     }
     gb.sync();
@@ -516,12 +552,7 @@ k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
         DotAcc<VT> acc;
         int slot = me;
         GRID_LOOP2(N, {
-            VT ps[3];
-            pair_sums<DIM>(g, t, i, ps);
-            VT q = c0 * t[i];
-            q = fma(-c1, ps[0], q);
-            q = fma(-c2, ps[1], q);
-            if (DIM == 3) q = fma(-c3, ps[2], q);
+            const VT q = stage2_at<DIM, VT>(g, t, i, c0, c1, c2, c3);
             bufW[slot] = q;
             acc.add(q, bufA[slot]);
             slot += kArnThreads;                // elements of this thread come in order
@@ -685,10 +716,11 @@ k_combine32b(int64_t N, const double *__restrict__ y0, const float *__restrict__
     GRID_LOOP(i, N) ynext[i] = y0[i] + ((double)d[i] - mean);
 }
 
-// FP64 -> FP32 copy (start vector of a mixed-precision Krylov run) and FP32 D.
+// FP64 -> FP32 copy y = x + shift (the start vector of a mixed-precision Krylov run with
+// shift 0; the FP32 stage coefficient J = D - eps^2 sigma with shift -eps^2 sigma).
 __global__ void __launch_bounds__(kThreads)
-k_to32(int64_t N, const double *__restrict__ x, float *__restrict__ y) {
-    GRID_LOOP(i, N) y[i] = (float)x[i];
+k_to32(int64_t N, const double *__restrict__ x, double shift, float *__restrict__ y) {
+    GRID_LOOP(i, N) y[i] = (float)(x[i] + shift);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -955,9 +987,9 @@ void launch_combine32(const Launch &L, int64_t N, const double *y0, const float 
     k_combine32b<<<L.blocks, kThreads, 0, L.stream>>>(N, y0, d, ynext, L.ctrl);
 }
 
-void launch_to32(const Launch &L, int64_t N, const double *x, float *y) {
+void launch_to32(const Launch &L, int64_t N, const double *x, float *y, double shift) {
     LaunchScope scope(L, CH_K_PREP);
-    k_to32<<<L.blocks, kThreads, 0, L.stream>>>(N, x, y);
+    k_to32<<<L.blocks, kThreads, 0, L.stream>>>(N, x, shift, y);
 }
 
 void launch_combine(const Launch &L, int64_t N, const double *y0, const double *v0,
