@@ -159,22 +159,28 @@ static int sparse_apply_A(const or_grid *g, const or_entry *in, int nin, or_entr
     return cnt;
 }
 
+/* Absolute sum of column j of A_hat_n, formed explicitly. */
+double or_column_abs_sum(const or_grid *g, const double *yn, long j) {
+    or_entry e[1], Ae[8], AAe[64], col[64];
+    double dj = Jdiag(yn[j]) + (g->eyre ? 1.0 : 0.0);
+    e[0].idx = j; e[0].val = 1.0;
+    int nA = sparse_apply_A(g, e, 1, Ae);          /* A e_j */
+    int nAA = sparse_apply_A(g, Ae, nA, AAe);      /* A A e_j */
+    /* column j of A_hat = A (D + eps^2 A) e_j = d_j A e_j + eps^2 A A e_j */
+    int nc = 0;
+    for (int k = 0; k < nA; ++k) nc = add_entry(col, nc, Ae[k].idx, dj * Ae[k].val);
+    for (int k = 0; k < nAA; ++k)
+        nc = add_entry(col, nc, AAe[k].idx, g->eps * g->eps * AAe[k].val);
+    double sum = 0.0;
+    for (int k = 0; k < nc; ++k) sum += fabs(col[k].val);
+    return sum;
+}
+
 double or_lambda_max(const or_grid *g, const double *yn) {
     long N = or_N(g);
     double best = 0.0;
-    or_entry e[1], Ae[8], AAe[64], col[64];
     for (long j = 0; j < N; ++j) {
-        double dj = Jdiag(yn[j]) + (g->eyre ? 1.0 : 0.0);
-        e[0].idx = j; e[0].val = 1.0;
-        int nA = sparse_apply_A(g, e, 1, Ae);          /* A e_j */
-        int nAA = sparse_apply_A(g, Ae, nA, AAe);      /* A A e_j */
-        /* column j of A_hat = A (D + eps^2 A) e_j = d_j A e_j + eps^2 A A e_j */
-        int nc = 0;
-        for (int k = 0; k < nA; ++k) nc = add_entry(col, nc, Ae[k].idx, dj * Ae[k].val);
-        for (int k = 0; k < nAA; ++k)
-            nc = add_entry(col, nc, AAe[k].idx, g->eps * g->eps * AAe[k].val);
-        double sum = 0.0;
-        for (int k = 0; k < nc; ++k) sum += fabs(col[k].val);
+        double sum = or_column_abs_sum(g, yn, j);
         if (sum > best) best = sum;
     }
     return best;

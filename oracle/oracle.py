@@ -83,6 +83,7 @@ def lib():
                 "or_ghat": (None, [G, _D, _D]),
                 "or_jacvec": (None, [G, _D, _D, _D]),
                 "or_lambda_max": (C.c_double, [G, _D]),
+                "or_column_abs_sum": (C.c_double, [G, _D, C.c_long]),
                 "or_cheb_order": (C.c_int, [C.c_double, C.c_double]),
                 "or_lim_order": (C.c_int, [C.c_int, np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")]),
                 "or_lim_step": (C.c_int, [G, _D, C.c_double, _D, C.POINTER(C.c_double),
@@ -160,6 +161,11 @@ def jacvec(g: Grid, y, v):
 
 def lambda_max(g: Grid, y) -> float:
     return lib().or_lambda_max(g.ptr(), g._vec(y))
+
+
+def column_abs_sum(g: Grid, y, j: int) -> float:
+    """Absolute sum of column j of A_hat_n (Fig. 1 step 1 for one column)."""
+    return lib().or_column_abs_sum(g.ptr(), g._vec(y), int(j))
 
 
 def cheb_order(tau: float, lmax: float) -> int:

@@ -86,6 +86,17 @@ def test_lambda_max_is_dense_one_norm(oracle, dim, n, eyre):
     assert abs(oracle.lambda_max(g, y) - ref) <= 1e-13 * ref
 
 
+@pytest.mark.parametrize("dim,n", [(2, (6, 5)), (3, (4, 5, 6))])
+def test_column_abs_sum_is_dense_column_sum(oracle, dim, n):
+    """One column of Fig. 1 step 1: the absolute sum of every column of A_hat."""
+    eps = 0.07
+    g = oracle.Grid(dim, n, eps)
+    y = inputs.initial_state(n, 22, -1.1, 1.1)
+    ref = np.abs(dense_Ahat(n, y, eps, False)).sum(axis=0)
+    got = np.array([oracle.column_abs_sum(g, y, j) for j in range(ref.size)])
+    assert np.allclose(got, ref, rtol=1e-13, atol=0)
+
+
 def _golden_counts():
     path = os.path.join(os.path.dirname(__file__), "golden", "paper_lim_counts.txt")
     rows = []
