@@ -169,14 +169,14 @@ def run_reference(args, rank, world):
 def run_batch_workload(args, rank, world, dist):
     import numpy as np
     import torch
-    from paper_2502_14589_gb300 import build, ch, inputs
+    from paper_2502_14589_gb300 import build, ch, inputs, replicas
     build.build()
     wl = dict(inputs.WORKLOADS[args.workload])
     if args.t_final is not None:
         wl["T"] = args.t_final
     count = wl["count"]
     sides, eps = inputs.batch_descriptors(count, seed=0)
-    y0s = [inputs.initial_state((int(n), int(n)), 1 + i + 1000 * rank, wl["lo"], wl["hi"])
+    y0s = [inputs.initial_state((int(n), int(n)), replicas.batch_instance_seed(rank, i), wl["lo"], wl["hi"])
            for i, n in enumerate(sides)]
     Ns = np.array([int(n) * int(n) for n in sides])
     stream = torch.cuda.current_stream()
@@ -194,6 +194,9 @@ def run_batch_workload(args, rank, world, dist):
             y.copy_(y0); ch.ch_integrate_batch(h, prm, y, count)
         torch.cuda.synchronize()
         ms, ops = 0.0, 0
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
         for _ in range(reps):
             y.copy_(y0)
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
@@ -202,6 +205,10 @@ def run_batch_workload(args, rank, world, dist):
             e1.record(stream); e1.synchronize()
             ms += e0.elapsed_time(e1)
             ops += int(sum(Ns[i] * (st[i]["matvecs"] + st[i]["rhs_evals"]) for i in range(count)))
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ms, ops = replicas.combine(dist, ms, ops, "cuda")
         yh = y.cpu().numpy()
         out[name] = {"ms": ms / reps, "value": ops / (ms * 1e-3), "chunk_len": chunk,
                      "steps_max": max(x["steps"] for x in st), "steps_sum": sum(x["steps"] for x in st),
@@ -254,7 +261,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_2502_14589_gb300 import build, ch, inputs
+    from paper_2502_14589_gb300 import build, ch, inputs, replicas
     build.build()
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -263,7 +270,7 @@ def main():
         wl["T"] = args.t_final
     n = [wl["n"]] * wl["dim"]
     N = int(np.prod(n))
-    y0_host = inputs.initial_state(n, rank, wl["lo"], wl["hi"], wl["mean"])
+    y0_host = inputs.initial_state(n, replicas.instance_seed(rank), wl["lo"], wl["hi"], wl["mean"])
     y0 = torch.from_numpy(y0_host).to(dev)
     y = torch.empty_like(y0)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -317,14 +324,7 @@ def main():
     clk = clocks.stop() if rank == 0 else None
     launches = ch.ch_kernel_launches(G.h) - launches0
     _, _, counts = ch.ch_timing_read(G.h)
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        o = torch.tensor([float(ops)], dtype=torch.float64, device=dev)
-        dist.all_reduce(o, op=dist.ReduceOp.SUM)
-        ops = float(o.item())
+    total_ms, ops = replicas.combine(dist, sum(step_ms), ops, dev)
     value = ops / (total_ms * 1e-3)
     ttt = {}
     for s in ("ee2", "lim"):
