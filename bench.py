@@ -356,6 +356,8 @@ def main():
                  "ee2_rel_err_at_T_vs_fp64": err, "steps": stm["steps"], "matvecs": stm["matvecs"],
                  "ops_per_s": N * (stm["matvecs"] + stm["rhs_evals"]) / (ms_m * 1e-3),
                  "mass_drift": float(abs(ym.mean() - y0.mean()))}
+        if not args.no_roofline:        # one Arnoldi iteration (j = 10) on the FP32 basis
+            mixed["arnoldi_j10_us"] = ch.ch_bench_kernel(Gm.h, "arnoldi", 50)["avg_us"]
         Gm.close()
 
     # ---- end to end through the C ABI with host buffers ----------------------------------

@@ -77,6 +77,8 @@ struct ch_grid {
     int use_graphs;
     int fused_arnoldi;            // 1: one cooperative launch per Arnoldi iteration
     int arn_blocks;               // its grid
+    float2 *gpart;                // mixed grids: reduction scratch of the Gram-corrected iteration
+    double *gram;                 // mixed grids: Gram matrix of the Krylov basis
     // device workspace
     double *D, *G, *t, *q;        // per-step coefficients and stage scratch
     double *F[2];                 // rhs buffers; F[cur] is basis column 0 of a Krylov run
@@ -183,6 +185,14 @@ static void queue_block(ch_grid *g, const Launch &L, VT *slot0, VT *V, const VT 
     auto W = [&](int c) -> VT * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * g->ldv; };
     for (int j = j0; j <= j1; ++j) {
         if (g->fused_arnoldi) {
+            if constexpr (sizeof(VT) == 4) {
+                if (j <= ch::kGsMaxJ) {
+                    ch::launch_arnoldi_gmgs(L, g->arn_blocks, g->g, slot0, V, g->ldv, Dm, t, g->H, ldh, j,
+                                            g->gpart, g->gram, g->mmax_cap + 1);
+                    if (mmax > 63) ch::launch_phi(L, g->H, ldh, j, mmax, g->u, g->phi_scratch);
+                    continue;
+                }
+            }
             ch::launch_arnoldi<VT>(L, g->arn_blocks, g->g, slot0, V, g->ldv, Dm, t, g->H, ldh, j);
             if (mmax > 63) ch::launch_phi(L, g->H, ldh, j, mmax, g->u, g->phi_scratch);
             continue;
@@ -526,10 +536,12 @@ ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us
             break;
         case CH_K_ARNOLDI: {  // one whole Arnoldi iteration with j = min(10, capacity) passes
             const int j = std::min(10, g->mmax_cap);
-            if (mixed) ch::launch_arnoldi<float>(Lc, g->arn_blocks, g->g, g->Wf[0], g->Vf, g->ldv, g->Df, g->tf, g->H, g->mmax_cap, j);
+            if (mixed) ch::launch_arnoldi_gmgs(Lc, g->arn_blocks, g->g, g->Wf[0], g->Vf, g->ldv, g->Df, g->tf,
+                                               g->H, g->mmax_cap, j, g->gpart, g->gram, g->mmax_cap + 1);
             else ch::launch_arnoldi<double>(Lc, g->arn_blocks, g->g, g->F[0], g->V, g->ldv, g->D, g->t, g->H, g->mmax_cap, j);
-            bytes = (5.0 + j) * vb * N;
-            flops = ((1 + 3.0 * d) + (3 + 3.0 * d) + 4.0 * j) * N;
+            bytes = mixed ? (6.0 + 3.0 * j) * vb * N : (5.0 + j) * vb * N;
+            flops = mixed ? ((1 + 3.0 * d) + (1 + 3.0 * d) + 6.0 * j + 2.0) * N
+                          : ((1 + 3.0 * d) + (3 + 3.0 * d) + 4.0 * j) * N;
             instr = mixed ? 0 : ((1 + 2.0 * d) + (2 + 2.0 * d) + 2.0 * j) * N;
             break;
         }
@@ -669,6 +681,10 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
             e = cudaMalloc((void **)a.p, a.bytes);
             if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of FP32 basis", e); }
         }
+        e = cudaMalloc((void **)&g->gpart, sizeof(float2) * 2 * (ch::kGsMaxJ + 1) * (size_t)std::max(g->arn_blocks, 1));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&g->gram, sizeof(double) * (size_t)(mmax_capacity + 1) * (mmax_capacity + 1));
+        if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of Gram workspace", e); }
     }
     e = cudaMalloc((void **)&g->ctrl, sizeof(Ctrl));
     if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of control block", e); }
@@ -699,6 +715,8 @@ ch_status ch_destroy_grid(ch_grid *g) {
     float *fbufs[] = {g->Vf, g->Wf[0], g->Wf[1], g->Df, g->tf};
     for (float *b : fbufs)
         if (b) cudaFree(b);
+    if (g->gpart) cudaFree(g->gpart);
+    if (g->gram) cudaFree(g->gram);
     if (g->ctrl) cudaFree(g->ctrl);
     if (g->hctrl) cudaFreeHost(g->hctrl);
     if (g->hflag) cudaFreeHost(g->hflag);

@@ -599,6 +599,310 @@ k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Arnoldi iteration j for an FP32 basis with Gram-corrected modified Gram-Schmidt.
+//
+// Fig. 2 lines 5-8 give h_kj = v_k . w^(k-1) with w^(k-1) = w - sum_{i<k} h_ij v_i, i.e.
+//     h_kj = c_k - sum_{i<k} G_ki h_ij,   c_k = v_k . w,   G_ki = v_k . v_i   (i < k),
+// an identity for any computed basis, so these are the modified Gram-Schmidt coefficients
+// (not classical Gram-Schmidt, which drops the G terms).  The c_k of all k come from one
+// sweep and one grid-wide reduction; the G row of a new vector comes from the reduction
+// that also gives its norm.  An iteration thus needs 3 grid synchronisations instead of
+// j + 2, which is what bounds the FP32 iteration (its arithmetic is cheap).  The rounding
+// differs from the sequential passes (the FP64 path keeps them, for parity with the oracle).
+//
+//   stage 1, stage 2 (w = A_hat v_j, into the W_{j+1} slot)          | barrier after stage 1
+//   sweep A: c_k = v_k . w, k = 1..j                                  | round A
+//   forward substitution for h_kj (warp 0 of every block, identical)
+//   sweep B1: w' = w - sum_k h_kj v_k (order k = 1..j);
+//   sweep B2: v_k . w' (k = 1..j) and ||w'||^2                        | round B
+//   h_{j+1,j} = ||w'||, gam_j = 1 / h_{j+1,j}, G_{j+1,k} = v_k . w' / h_{j+1,j}
+//
+// Per-thread dot products are compensated FP32 pairs (DotAcc<float>); block and grid sums
+// add those pairs in double-float FP32 arithmetic in a fixed order (FP64 adds would cost 64
+// cycles each on GB300), so results are deterministic.
+// ---------------------------------------------------------------------------------------
+constexpr int kGsChunk = 8;                          // dot products per sweep chunk
+constexpr int kGsSmemBytes = kGsChunk * kArnThreads * (int)sizeof(float2);
+
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    const float hi = __fadd_rn(s, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+
+// Block sums of nk <= kGsChunk per-thread pairs acc[q] (1024 threads), written as pairs
+// to out[q] by the warps q.  red holds kGsChunk x 1024 pairs.
+__device__ __forceinline__ void gs_block_sums(const DotAcc<float> (&acc)[kGsChunk], int nk,
+                                              float2 *red, float2 *out) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < kGsChunk; ++q) red[q * kArnThreads + tid] = make_float2(acc[q].s, acc[q].c);
+    __syncthreads();
+    // level 1: value q = tid / 128; thread adds 8 consecutive pairs of its value
+    const int q1 = tid >> 7, sg = tid & 127;
+    float2 a = make_float2(0.f, 0.f);
+    if (q1 < nk) {
+        const float2 *p = red + q1 * kArnThreads + sg * 8;
+        a = ff_add(ff_add(ff_add(p[0], p[1]), ff_add(p[2], p[3])), ff_add(ff_add(p[4], p[5]), ff_add(p[6], p[7])));
+    }
+    __syncthreads();
+    if (q1 < nk) red[q1 * kArnThreads + sg] = a;
+    __syncthreads();
+    // level 2: warp q adds the 128 partials of value q (4 per lane, then a shuffle tree)
+    const int wq = tid >> 5, lane = tid & 31;
+    if (wq < nk) {
+        const float2 *p = red + wq * kArnThreads + lane * 4;
+        float2 b = ff_add(ff_add(p[0], p[1]), ff_add(p[2], p[3]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float2 c;
+            c.x = __shfl_down_sync(0xffffffffu, b.x, o);
+            c.y = __shfl_down_sync(0xffffffffu, b.y, o);
+            b = ff_add(b, c);
+        }
+        if (lane == 0) out[wq] = b;
+    }
+    __syncthreads();
+}
+
+// Grid sum of value q over the G block pairs part[q * G + b], by warp q (pairs added in a
+// fixed order), as a double in lane 0.
+__device__ __forceinline__ double gs_grid_sum_warp(const float2 *part, int q) {
+    const unsigned G = gridDim.x, lane = threadIdx.x & 31;
+    float2 v[kMaxArnBlocks / 32];
+#pragma unroll
+    for (int s = 0; s < kMaxArnBlocks / 32; ++s) {
+        const unsigned b = lane + 32u * s;
+        v[s] = make_float2(0.f, 0.f);
+        if (b < G) {
+            const float2 x = __ldcg(reinterpret_cast<const float2 *>(part) + (size_t)q * G + b);
+            v[s] = x;
+        }
+    }
+    float2 a = v[0];
+#pragma unroll
+    for (int s = 1; s < kMaxArnBlocks / 32; ++s) a = ff_add(a, v[s]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float2 c;
+        c.x = __shfl_down_sync(0xffffffffu, a.x, o);
+        c.y = __shfl_down_sync(0xffffffffu, a.y, o);
+        a = ff_add(a, c);
+    }
+    return (double)a.x + (double)a.y;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kArnThreads, 1)
+k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t ldv,
+               const float *__restrict__ D, float *__restrict__ t, double *H, int ldh, int j,
+               float2 *gpart, double *gram, int ldg, Ctrl *ctrl) {
+    if (!ctrl->active) return;                  // same value in every block
+    extern __shared__ __align__(16) unsigned char dyn[];
+    float2 *red = reinterpret_cast<float2 *>(dyn);
+    __shared__ float2 bout[kGsChunk];
+    __shared__ double cs[kGsMaxJ + 1];          // grid sums of the round
+    __shared__ float gs[kGsMaxJ][kGsMaxJ + 1];  // G_ki (k > i), 0-based
+    __shared__ float as[kGsMaxJ];               // update coefficients h_kj gam_{k-1}
+    auto W = [&](int c) -> float * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * ldv; };
+    GridBarrier gb(&ctrl->bar, &ctrl->status);
+    const unsigned N = (unsigned)g.N;
+    const unsigned G = gridDim.x;
+    float *w = W(j + 1);
+    float2 *pA = gpart, *pB = gpart + (size_t)(kGsMaxJ + 1) * G;
+    // Gram rows of v_2..v_j against the earlier vectors (written by iterations 1..j-1)
+    for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
+        const int k = e / j, i = e % j;
+        gs[k][i] = i < k ? (float)gram[(size_t)k * ldg + i] : 0.f;
+    }
+    // ---- stage 1: t = J x + sum_a kap_a ((x - x_{+a}) + (x - x_{-a}))
+    {
+        const float *x = W(j);
+        const float k0 = (float)g.kap[0], k1 = (float)g.kap[1], k2 = (float)g.kap[2];
+        GRID_LOOP2(N, {
+            t[i] = stage1_at<DIM, float>(g, x, D, i, k0, k1, k2);
+        })
+    }
+    gb.sync();
+    // Stage 2 and the sweeps visit the points in groups of four consecutive ones (group q:
+    // points 4q..4q+3, groups strided over the grid's threads; the last group may be
+    // partial), so every column is read with 16-byte loads and a thread keeps the same
+    // points from stage 2 to the end of the iteration: w needs no barrier between them.
+    const unsigned NG = (N + 3u) / 4u, S = G * kArnThreads;
+    const unsigned q0 = blockIdx.x * kArnThreads + threadIdx.x;
+    auto ld4 = [&](const float *col, unsigned q, bool full) -> float4 {
+        if (full) return reinterpret_cast<const float4 *>(col)[q];
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4u * q + 0u < N) r.x = col[4u * q + 0u];
+        if (4u * q + 1u < N) r.y = col[4u * q + 1u];
+        if (4u * q + 2u < N) r.z = col[4u * q + 2u];
+        return r;                                   // a partial group has at most 3 points
+    };
+    // ---- stage 2: w = gam_j sum_a s_a ((t - t_{+a}) + (t - t_{-a})) = A_hat v_j
+    {
+        const double gam = ctrl->gam[j - 1];
+        const float c0 = (float)(gam * g.sigma), c1 = (float)(gam * g.s[0]), c2 = (float)(gam * g.s[1]),
+                    c3 = (float)(gam * g.s[2]);
+        for (unsigned q = q0; q < NG; q += S)
+#pragma unroll
+            for (unsigned e = 0; e < 4u; ++e)
+                if (4u * q + e < N) w[4u * q + e] = stage2_at<DIM, float>(g, t, 4u * q + e, c0, c1, c2, c3);
+    }
+    // ---- sweep A: W_k . w for k = 1..j, kGsChunk columns per pass over the points (their
+    //      16-byte loads issued together, so the sweep is bound by bandwidth, not latency)
+    for (int k0 = 1; k0 <= j; k0 += kGsChunk) {
+        const int nk = min(kGsChunk, j - k0 + 1);
+        DotAcc<float> acc[kGsChunk];
+        for (unsigned q = q0; q < NG; q += S) {
+            const bool full = 4u * q + 3u < N;
+            const float4 wv = ld4(w, q, full);
+#pragma unroll
+            for (int h = 0; h < kGsChunk; h += 4) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    v[u] = h + u < nk ? ld4(W(k0 + h + u), q, full) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (h + u < nk) {
+                        acc[h + u].add(wv.x, v[u].x);
+                        acc[h + u].add(wv.y, v[u].y);
+                        acc[h + u].add(wv.z, v[u].z);
+                        acc[h + u].add(wv.w, v[u].w);
+                    }
+            }
+        }
+        gs_block_sums(acc, nk, red, bout);
+        if (threadIdx.x < nk) pA[(size_t)(k0 - 1 + threadIdx.x) * G + blockIdx.x] = bout[threadIdx.x];
+    }
+    gb.sync();
+    {
+        const int wq = threadIdx.x >> 5;
+        if (wq < j) {
+            const double sum = gs_grid_sum_warp(pA, wq);
+            if ((threadIdx.x & 31) == 0) cs[wq] = ctrl->gam[wq] * sum;     // c_k = v_k . w
+        }
+    }
+    __syncthreads();
+    // ---- forward substitution h_k = c_k - sum_{i<k} G_ki h_i (lane k-1 of warp 0).  The
+    //      corrections are small next to c_k and are accumulated in FP32; h_k is FP64.
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        const double r = l < j ? cs[l] : 0.0;
+        const float rf = (float)r;
+        float corr = 0.f;
+        for (int i = 0; i < j; ++i) {
+            const float hi = __shfl_sync(0xffffffffu, __fsub_rn(rf, corr), i);
+            if (l > i && l < j) corr = __fmaf_rn(gs[l][i], hi, corr);
+        }
+        if (l < j) {
+            const double h = r - (double)corr;
+            as[l] = (float)(h * ctrl->gam[l]);
+            if (blockIdx.x == 0) H[l * ldh + (j - 1)] = h;
+        }
+    }
+    __syncthreads();
+    // ---- sweep B1: w' = w - sum_k h_kj v_k;  sweep B2: W_k . w' and ||w'||^2
+    for (unsigned q = q0; q < NG; q += S) {
+        const bool full = 4u * q + 3u < N;
+        float4 x = ld4(w, q, full);
+        for (int k0 = 1; k0 <= j; k0 += 4) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                v[u] = k0 + u <= j ? ld4(W(k0 + u), q, full) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k0 + u <= j) {
+                    const float a_ = -as[k0 + u - 1];
+                    x.x = __fmaf_rn(a_, v[u].x, x.x);
+                    x.y = __fmaf_rn(a_, v[u].y, x.y);
+                    x.z = __fmaf_rn(a_, v[u].z, x.z);
+                    x.w = __fmaf_rn(a_, v[u].w, x.w);
+                }
+        }
+        if (full) {
+            reinterpret_cast<float4 *>(w)[q] = x;
+        } else {
+            if (4u * q + 0u < N) w[4u * q + 0u] = x.x;
+            if (4u * q + 1u < N) w[4u * q + 1u] = x.y;
+            if (4u * q + 2u < N) w[4u * q + 2u] = x.z;
+        }
+    }
+    for (int k0 = 1; k0 <= j + 1; k0 += kGsChunk) {
+        const int nk = min(kGsChunk, j + 2 - k0);
+        DotAcc<float> acc[kGsChunk];
+        for (unsigned q = q0; q < NG; q += S) {
+            const bool full = 4u * q + 3u < N;
+            const float4 wv = ld4(w, q, full);
+#pragma unroll
+            for (int h = 0; h < kGsChunk; h += 4) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    v[u] = h + u < nk ? (k0 + h + u <= j ? ld4(W(k0 + h + u), q, full) : wv)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (h + u < nk) {
+                        acc[h + u].add(wv.x, v[u].x);
+                        acc[h + u].add(wv.y, v[u].y);
+                        acc[h + u].add(wv.z, v[u].z);
+                        acc[h + u].add(wv.w, v[u].w);
+                    }
+            }
+        }
+        gs_block_sums(acc, nk, red, bout);
+        if (threadIdx.x < nk) pB[(size_t)(k0 - 1 + threadIdx.x) * G + blockIdx.x] = bout[threadIdx.x];
+    }
+    gb.sync();
+    {
+        const int wq = threadIdx.x >> 5;
+        if (wq <= j) {
+            const double sum = gs_grid_sum_warp(pB, wq);
+            if ((threadIdx.x & 31) == 0) cs[wq] = sum;
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double nrm2 = cs[j];
+        const double hn = sqrt(nrm2);                         // h_{j+1,j} (Fig. 2 line 9)
+        ctrl->hnext2 = nrm2;
+        H[j * ldh + (j - 1)] = hn;
+        ctrl->gam[j] = 1.0 / hn;
+        for (int k = 0; k < j; ++k)                           // G_{j+1,k} = v_{j+1} . v_k
+            gram[(size_t)j * ldg + k] = ctrl->gam[k] * cs[k] / hn;
+    }
+}
+
+void launch_arnoldi_gmgs(const Launch &L, int blocks, const Geom &g, float *slot0, float *V,
+                         int64_t ldv, const float *D, float *t, double *H, int ldh, int j,
+                         float2 *gpart, double *gram, int ldg) {
+    LaunchScope scope(L, CH_K_ARNOLDI);
+    {   // stages as the MGS form; j dots, j update fma and j + 1 dots (FP32, counted as flops)
+        const double N = (double)g.N, d = g.dim;
+        scope.work(((1.0 + 3.0 * d) + (1.0 + 3.0 * d) + 6.0 * j + 2.0) * N, (6.0 + 3.0 * j) * 4.0 * N);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks, 1, 1);
+    cfg.blockDim = dim3(kArnThreads, 1, 1);
+    cfg.dynamicSmemBytes = kGsSmemBytes;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (g.dim == 3)
+        cudaLaunchKernelEx(&cfg, k_arnoldi_gmgs<3>, g, slot0, V, ldv, D, t, H, ldh, j, gpart, gram, ldg, L.ctrl);
+    else
+        cudaLaunchKernelEx(&cfg, k_arnoldi_gmgs<2>, g, slot0, V, ldv, D, t, H, ldh, j, gpart, gram, ldg, L.ctrl);
+}
+
 template <typename VT>
 int arnoldi_blocks(int dim, int64_t N) {
     int per_sm = 0, dev = 0, sms = 0;
@@ -656,6 +960,11 @@ int arnoldi_setup() {
                          (const void *)k_arnoldi_res<2, float>, (const void *)k_arnoldi_res<3, float>};
     for (const void *f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kArnResMaxBytes);
+        if (e != cudaSuccess) return (int)e;
+    }
+    const void *gfns[] = {(const void *)k_arnoldi_gmgs<2>, (const void *)k_arnoldi_gmgs<3>};
+    for (const void *f : gfns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kGsSmemBytes);
         if (e != cudaSuccess) return (int)e;
     }
     return 0;
