@@ -539,7 +539,7 @@ ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us
             if (mixed) ch::launch_arnoldi_gmgs(Lc, g->arn_blocks, g->g, g->Wf[0], g->Vf, g->ldv, g->Df, g->tf,
                                                g->H, g->mmax_cap, j, g->gpart, g->gram, g->mmax_cap + 1);
             else ch::launch_arnoldi<double>(Lc, g->arn_blocks, g->g, g->F[0], g->V, g->ldv, g->D, g->t, g->H, g->mmax_cap, j);
-            bytes = mixed ? (6.0 + 3.0 * j) * vb * N : (5.0 + j) * vb * N;
+            bytes = mixed ? (6.0 + 2.0 * j) * vb * N : (5.0 + j) * vb * N;
             flops = mixed ? ((1 + 3.0 * d) + (1 + 3.0 * d) + 6.0 * j + 2.0) * N
                           : ((1 + 3.0 * d) + (3 + 3.0 * d) + 4.0 * j) * N;
             instr = mixed ? 0 : ((1 + 2.0 * d) + (2 + 2.0 * d) + 2.0 * j) * N;
@@ -681,7 +681,7 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
             e = cudaMalloc((void **)a.p, a.bytes);
             if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of FP32 basis", e); }
         }
-        e = cudaMalloc((void **)&g->gpart, sizeof(float2) * 2 * (ch::kGsMaxJ + 1) * (size_t)std::max(g->arn_blocks, 1));
+        e = cudaMalloc((void **)&g->gpart, sizeof(float2) * 3 * (ch::kGsMaxJ + 1) * (size_t)std::max(g->arn_blocks, 1));
         if (e == cudaSuccess)
             e = cudaMalloc((void **)&g->gram, sizeof(double) * (size_t)(mmax_capacity + 1) * (mmax_capacity + 1));
         if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of Gram workspace", e); }

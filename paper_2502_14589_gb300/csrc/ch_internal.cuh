@@ -228,9 +228,9 @@ void launch_arnoldi(const Launch &L, int blocks, const Geom &g, VT *slot0, VT *V
 template <typename VT>
 int arnoldi_blocks(int dim, int64_t N);
 // FP32-basis Arnoldi iteration j <= kGsMaxJ with Gram-corrected modified Gram-Schmidt
-// (3 grid synchronisations).  gpart: 2 x (kGsMaxJ + 1) x blocks float2 of scratch; gram:
+// (3 grid synchronisations).  gpart: 3 x (kGsMaxJ + 1) x blocks float2 of scratch; gram:
 // the Gram matrix of the normalised basis, row k (vector k + 1) at gram + k ldg, rows
-// 1..j-1 written by the earlier iterations of the same Krylov run, row j by this one.
+// 1..j-2 written by the earlier iterations of the same Krylov run, row j - 1 by this one.
 constexpr int kGsMaxJ = 31;
 void launch_arnoldi_gmgs(const Launch &L, int blocks, const Geom &g, float *slot0, float *V,
                          int64_t ldv, const float *D, float *t, double *H, int ldh, int j,

@@ -126,6 +126,13 @@ template <> struct DotAcc<float> {
         s = t;
         c = __fadd_rn(c, __fadd_rn(err, e));
     }
+    // add a value (a short FP32 dot product) with the compensated two-sum only
+    __device__ __forceinline__ void add_value(float p) {
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+        s = t;
+    }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
@@ -605,25 +612,26 @@ k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
 // Fig. 2 lines 5-8 give h_kj = v_k . w^(k-1) with w^(k-1) = w - sum_{i<k} h_ij v_i, i.e.
 //     h_kj = c_k - sum_{i<k} G_ki h_ij,   c_k = v_k . w,   G_ki = v_k . v_i   (i < k),
 // an identity for any computed basis, so these are the modified Gram-Schmidt coefficients
-// (not classical Gram-Schmidt, which drops the G terms).  The c_k of all k come from one
-// sweep and one grid-wide reduction; the G row of a new vector comes from the reduction
-// that also gives its norm.  An iteration thus needs 3 grid synchronisations instead of
-// j + 2, which is what bounds the FP32 iteration (its arithmetic is cheap).  The rounding
-// differs from the sequential passes (the FP64 path keeps them, for parity with the oracle).
+// (not classical Gram-Schmidt, which drops the G terms).  All c_k, and the Gram row of the
+// newest vector v_j, come from one sweep over the basis and one grid-wide reduction; the
+// update and the new norm from a second sweep.  An iteration needs 3 grid synchronisations
+// instead of j + 2, which is what bounds the FP32 iteration (its arithmetic is cheap).  The
+// rounding differs from the sequential passes (the FP64 path keeps them, for parity with
+// the oracle).
 //
-//   stage 1, stage 2 (w = A_hat v_j, into the W_{j+1} slot)          | barrier after stage 1
-//   sweep A: c_k = v_k . w, k = 1..j                                  | round A
+//   stage 1, stage 2 (w = A_hat v_j, into the W_{j+1} slot)      | barrier after stage 1
+//   round A: c_k = v_k . w (k = 1..j), G_ji = v_j . v_i (i < j)   | grid reduction
 //   forward substitution for h_kj (warp 0 of every block, identical)
-//   sweep B1: w' = w - sum_k h_kj v_k (order k = 1..j);
-//   sweep B2: v_k . w' (k = 1..j) and ||w'||^2                        | round B
-//   h_{j+1,j} = ||w'||, gam_j = 1 / h_{j+1,j}, G_{j+1,k} = v_k . w' / h_{j+1,j}
+//   round B: w' = w - sum_k h_kj v_k and ||w'||^2                 | grid reduction
+//   h_{j+1,j} = ||w'||, gam_j = 1 / h_{j+1,j}
 //
 // Per-thread dot products are compensated FP32 pairs (DotAcc<float>); block and grid sums
 // add those pairs in double-float FP32 arithmetic in a fixed order (FP64 adds would cost 64
 // cycles each on GB300), so results are deterministic.
 // ---------------------------------------------------------------------------------------
-constexpr int kGsChunk = 8;                          // dot products per sweep chunk
-constexpr int kGsSmemBytes = kGsChunk * kArnThreads * (int)sizeof(float2);
+constexpr int kGsChunk = 8;                          // values per block reduction
+constexpr int kGsSmemBytes = kGsChunk * kArnThreads * (int)sizeof(float2)      // block sums
+                             + 4 * kArnThreads * (int)sizeof(float4);             // w, v_j cache
 
 __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
     const float s = __fadd_rn(a.x, b.x);
@@ -696,6 +704,37 @@ __device__ __forceinline__ double gs_grid_sum_warp(const float2 *part, int q) {
     return (double)a.x + (double)a.y;
 }
 
+// Difference sums d_a = (x - x_{+a}) + (x - x_{-a}) of the four consecutive points 4q..4q+3
+// (one row when n0 % 4 == 0), from 16-byte loads of the point's row and of the neighbouring
+// rows (planes) plus two scalars across the row ends; the same operations per point as
+// pair_diffs, so results are identical to the scalar stages.
+template <int DIM>
+__device__ __forceinline__ void group_diffs(const Geom &g, const float *__restrict__ x, unsigned q,
+                                            float4 &xc, float4 (&d)[3]) {
+    const unsigned n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    const unsigned i = 4u * q, c0 = i % n0, r = i / n0, c1 = r % n1;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const unsigned r4 = n0 / 4u;                                  // float4s per row
+    xc = x4[q];
+    const float xl = x[c0 == 0u ? i + n0 - 1u : i - 1u];
+    const float xr = x[c0 + 4u == n0 ? i + 4u - n0 : i + 4u];
+    d[0] = make_float4((xc.x - xc.y) + (xc.x - xl), (xc.y - xc.z) + (xc.y - xc.x),
+                       (xc.z - xc.w) + (xc.z - xc.y), (xc.w - xr) + (xc.w - xc.z));
+    const float4 yp = x4[c1 + 1u == n1 ? q - (n1 - 1u) * r4 : q + r4];
+    const float4 ym = x4[c1 == 0u ? q + (n1 - 1u) * r4 : q - r4];
+    d[1] = make_float4((xc.x - yp.x) + (xc.x - ym.x), (xc.y - yp.y) + (xc.y - ym.y),
+                       (xc.z - yp.z) + (xc.z - ym.z), (xc.w - yp.w) + (xc.w - ym.w));
+    if (DIM == 3) {
+        const unsigned n2 = (unsigned)g.n[2], c2 = r / n1, p4 = r4 * n1;
+        const float4 zp = x4[c2 + 1u == n2 ? q - (n2 - 1u) * p4 : q + p4];
+        const float4 zm = x4[c2 == 0u ? q + (n2 - 1u) * p4 : q - p4];
+        d[2] = make_float4((xc.x - zp.x) + (xc.x - zm.x), (xc.y - zp.y) + (xc.y - zm.y),
+                           (xc.z - zp.z) + (xc.z - zm.z), (xc.w - zp.w) + (xc.w - zm.w));
+    } else {
+        d[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(kArnThreads, 1)
 k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t ldv,
@@ -704,36 +743,66 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
     if (!ctrl->active) return;                  // same value in every block
     extern __shared__ __align__(16) unsigned char dyn[];
     float2 *red = reinterpret_cast<float2 *>(dyn);
+    // at most two groups per thread (grids up to 8 points per thread): w and v_j stay in
+    // shared memory between stage 2 and the end of the iteration
+    float4 *wsm = reinterpret_cast<float4 *>(red + kGsChunk * kArnThreads);   // [2][1024]
+    float4 *xsm = wsm + 2 * kArnThreads;                                       // [2][1024]
+    __shared__ double gams[kGsMaxJ + 1];        // gam_0..gam_j
+    __shared__ float hsm[32];                   // h of the substitution sweeps
     __shared__ float2 bout[kGsChunk];
     __shared__ double cs[kGsMaxJ + 1];          // grid sums of the round
-    __shared__ float gs[kGsMaxJ][kGsMaxJ + 1];  // G_ki (k > i), 0-based
+    __shared__ float gs[kGsMaxJ][kGsMaxJ + 2];  // G_ki (k > i), 0-based; odd row stride: no bank conflicts
     __shared__ float as[kGsMaxJ];               // update coefficients h_kj gam_{k-1}
     auto W = [&](int c) -> float * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * ldv; };
     GridBarrier gb(&ctrl->bar, &ctrl->status);
     const unsigned N = (unsigned)g.N;
     const unsigned G = gridDim.x;
     float *w = W(j + 1);
-    float2 *pA = gpart, *pB = gpart + (size_t)(kGsMaxJ + 1) * G;
-    // Gram rows of v_2..v_j against the earlier vectors (written by iterations 1..j-1)
+    float2 *pA = gpart, *pB = gpart + (size_t)2 * (kGsMaxJ + 1) * G;
+    for (int e = threadIdx.x; e < j; e += blockDim.x) gams[e] = ctrl->gam[e];
+    // Gram rows of v_2..v_{j-1} against the earlier vectors (from iterations 2..j-1); the
+    // row of v_j comes from this iteration's round A
     for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
         const int k = e / j, i = e % j;
-        gs[k][i] = i < k ? (float)gram[(size_t)k * ldg + i] : 0.f;
+        gs[k][i] = (i < k && k < j - 1) ? (float)gram[(size_t)k * ldg + i] : 0.f;
     }
+    // The stages and the sweeps visit the points in groups of four consecutive ones (group
+    // q: points 4q..4q+3, groups strided over the grid's threads; the last group may be
+    // partial), so every column is read with 16-byte loads and a thread keeps the same
+    // points from stage 2 to the end of the iteration: w needs no barrier between them.
+    // Rows of a multiple of four points take whole groups in the stencil stages too.
+    const unsigned NG = (N + 3u) / 4u, S = G * kArnThreads;
+    const unsigned q0 = blockIdx.x * kArnThreads + threadIdx.x;
+    const bool rows4 = (g.n[0] & 3) == 0;
+    const bool res = NG <= 2u * S;
     // ---- stage 1: t = J x + sum_a kap_a ((x - x_{+a}) + (x - x_{-a}))
     {
         const float *x = W(j);
         const float k0 = (float)g.kap[0], k1 = (float)g.kap[1], k2 = (float)g.kap[2];
-        GRID_LOOP2(N, {
-            t[i] = stage1_at<DIM, float>(g, x, D, i, k0, k1, k2);
-        })
+        if (rows4) {
+            for (unsigned q = q0; q < NG; q += S) {
+                float4 xc, d[3];
+                group_diffs<DIM>(g, x, q, xc, d);
+                const float4 dq = reinterpret_cast<const float4 *>(D)[q];
+                float4 r;
+                r.x = dq.x * xc.x; r.y = dq.y * xc.y; r.z = dq.z * xc.z; r.w = dq.w * xc.w;
+                r.x = fmaf(k0, d[0].x, r.x); r.y = fmaf(k0, d[0].y, r.y);
+                r.z = fmaf(k0, d[0].z, r.z); r.w = fmaf(k0, d[0].w, r.w);
+                r.x = fmaf(k1, d[1].x, r.x); r.y = fmaf(k1, d[1].y, r.y);
+                r.z = fmaf(k1, d[1].z, r.z); r.w = fmaf(k1, d[1].w, r.w);
+                if (DIM == 3) {
+                    r.x = fmaf(k2, d[2].x, r.x); r.y = fmaf(k2, d[2].y, r.y);
+                    r.z = fmaf(k2, d[2].z, r.z); r.w = fmaf(k2, d[2].w, r.w);
+                }
+                reinterpret_cast<float4 *>(t)[q] = r;
+            }
+        } else {
+            GRID_LOOP2(N, {
+                t[i] = stage1_at<DIM, float>(g, x, D, i, k0, k1, k2);
+            })
+        }
     }
     gb.sync();
-    // Stage 2 and the sweeps visit the points in groups of four consecutive ones (group q:
-    // points 4q..4q+3, groups strided over the grid's threads; the last group may be
-    // partial), so every column is read with 16-byte loads and a thread keeps the same
-    // points from stage 2 to the end of the iteration: w needs no barrier between them.
-    const unsigned NG = (N + 3u) / 4u, S = G * kArnThreads;
-    const unsigned q0 = blockIdx.x * kArnThreads + threadIdx.x;
     auto ld4 = [&](const float *col, unsigned q, bool full) -> float4 {
         if (full) return reinterpret_cast<const float4 *>(col)[q];
         float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -747,135 +816,200 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
         const double gam = ctrl->gam[j - 1];
         const float c0 = (float)(gam * g.sigma), c1 = (float)(gam * g.s[0]), c2 = (float)(gam * g.s[1]),
                     c3 = (float)(gam * g.s[2]);
-        for (unsigned q = q0; q < NG; q += S)
+        if (rows4) {
+            for (unsigned q = q0, ri = 0; q < NG; q += S, ++ri) {
+                float4 tc, d[3];
+                group_diffs<DIM>(g, t, q, tc, d);
+                float4 r;
+                r.x = c1 * d[0].x; r.y = c1 * d[0].y; r.z = c1 * d[0].z; r.w = c1 * d[0].w;
+                r.x = fmaf(c2, d[1].x, r.x); r.y = fmaf(c2, d[1].y, r.y);
+                r.z = fmaf(c2, d[1].z, r.z); r.w = fmaf(c2, d[1].w, r.w);
+                if (DIM == 3) {
+                    r.x = fmaf(c3, d[2].x, r.x); r.y = fmaf(c3, d[2].y, r.y);
+                    r.z = fmaf(c3, d[2].z, r.z); r.w = fmaf(c3, d[2].w, r.w);
+                }
+                if (res) {
+                    wsm[ri * kArnThreads + threadIdx.x] = r;
+                    xsm[ri * kArnThreads + threadIdx.x] = reinterpret_cast<const float4 *>(W(j))[q];
+                } else {
+                    reinterpret_cast<float4 *>(w)[q] = r;
+                }
+            }
+        } else {
+            for (unsigned q = q0, ri = 0; q < NG; q += S, ++ri) {
+                float r[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (unsigned e = 0; e < 4u; ++e)
-                if (4u * q + e < N) w[4u * q + e] = stage2_at<DIM, float>(g, t, 4u * q + e, c0, c1, c2, c3);
+                for (unsigned e = 0; e < 4u; ++e)
+                    if (4u * q + e < N) r[e] = stage2_at<DIM, float>(g, t, 4u * q + e, c0, c1, c2, c3);
+                if (res) {
+                    wsm[ri * kArnThreads + threadIdx.x] = make_float4(r[0], r[1], r[2], r[3]);
+                    xsm[ri * kArnThreads + threadIdx.x] = ld4(W(j), q, 4u * q + 3u < N);
+                } else {
+#pragma unroll
+                    for (unsigned e = 0; e < 4u; ++e)
+                        if (4u * q + e < N) w[4u * q + e] = r[e];
+                }
+            }
+        }
     }
-    // ---- sweep A: W_k . w for k = 1..j, kGsChunk columns per pass over the points (their
-    //      16-byte loads issued together, so the sweep is bound by bandwidth, not latency)
-    for (int k0 = 1; k0 <= j; k0 += kGsChunk) {
-        const int nk = min(kGsChunk, j - k0 + 1);
-        DotAcc<float> acc[kGsChunk];
-        for (unsigned q = q0; q < NG; q += S) {
-            const bool full = 4u * q + 3u < N;
-            const float4 wv = ld4(w, q, full);
+    // ---- round A: one sweep gives c_k = v_k . w (k = 1..j) and the Gram row of the newest
+    //      basis vector, G_ji = v_j . v_i (i < j): each column is read once for both, four
+    //      columns per pass over the points with their 16-byte loads issued together.
+    //      Consecutive sweeps walk the basis in opposite directions, so each starts on the
+    //      columns read last, the likeliest to be still in L2.
+    const bool down = (j & 1) != 0;
+    const float *xj = W(j);
+    {
+        const int ncA = (j + 3) / 4;
+        for (int cA = 0; cA < ncA; ++cA) {
+            const int k0 = 1 + (down ? ncA - 1 - cA : cA) * 4;
+            const int nk = min(4, j - k0 + 1);
+            DotAcc<float> acc[kGsChunk];                  // [u]: W_k . w, [4 + u]: W_k . W_j
+            // the four products of a group are summed with plain FP32 FMAs (their rounding,
+            // random over the grid, stays far below the basis rounding after the exact
+            // cross-thread sums); only the running per-thread sum is compensated
+            auto dot4 = [](const float4 &a, const float4 &b) {
+                return __fmaf_rn(a.w, b.w, __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x))));
+            };
+            auto accum = [&](const float4 (&v)[4], const float4 &wv, const float4 &xv) {
 #pragma unroll
-            for (int h = 0; h < kGsChunk; h += 4) {
+                for (int u = 0; u < 4; ++u)
+                    if (u < nk) {
+                        acc[u].add_value(dot4(wv, v[u]));
+                        if (k0 + u < j) acc[4 + u].add_value(dot4(xv, v[u]));
+                    }
+            };
+            if (res) {   // both groups of the thread: all eight loads in flight at once
+                const unsigned qa = q0, qb = q0 + S;
+                const bool ha = qa < NG, hb = qb < NG;
+                const bool fa = 4u * qa + 3u < N, fb = 4u * qb + 3u < N;
+                float4 va[4], vb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    va[u] = (ha && u < nk) ? ld4(W(k0 + u), qa, fa) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    vb[u] = (hb && u < nk) ? ld4(W(k0 + u), qb, fb) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                if (ha) accum(va, wsm[threadIdx.x], xsm[threadIdx.x]);
+                if (hb) accum(vb, wsm[kArnThreads + threadIdx.x], xsm[kArnThreads + threadIdx.x]);
+            } else for (unsigned q = q0; q < NG; q += S) {
+                const bool full = 4u * q + 3u < N;
+                const float4 wv = ld4(w, q, full), xv = ld4(xj, q, full);
                 float4 v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    v[u] = h + u < nk ? ld4(W(k0 + h + u), q, full) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (h + u < nk) {
-                        acc[h + u].add(wv.x, v[u].x);
-                        acc[h + u].add(wv.y, v[u].y);
-                        acc[h + u].add(wv.z, v[u].z);
-                        acc[h + u].add(wv.w, v[u].w);
-                    }
+                    v[u] = u < nk ? ld4(W(k0 + u), q, full) : make_float4(0.f, 0.f, 0.f, 0.f);
+                accum(v, wv, xv);
             }
+            gs_block_sums(acc, kGsChunk, red, bout);
+            const int u = threadIdx.x & 3;
+            if (threadIdx.x < 4 && u < nk)
+                pA[(size_t)(k0 - 1 + u) * G + blockIdx.x] = bout[u];
+            else if (threadIdx.x >= 4 && threadIdx.x < 8 && u < nk && k0 + u < j)
+                pA[(size_t)(kGsMaxJ + 1 + k0 - 1 + u) * G + blockIdx.x] = bout[4 + u];
         }
-        gs_block_sums(acc, nk, red, bout);
-        if (threadIdx.x < nk) pA[(size_t)(k0 - 1 + threadIdx.x) * G + blockIdx.x] = bout[threadIdx.x];
     }
     gb.sync();
-    {
+    {   // slot k-1: W_k . w;  slot 32 + i - 1: W_i . W_j
         const int wq = threadIdx.x >> 5;
         if (wq < j) {
             const double sum = gs_grid_sum_warp(pA, wq);
-            if ((threadIdx.x & 31) == 0) cs[wq] = ctrl->gam[wq] * sum;     // c_k = v_k . w
+            if ((threadIdx.x & 31) == 0) cs[wq] = gams[wq] * sum;          // c_k = v_k . w
+        }
+        if (wq < j - 1) {
+            const double sum = gs_grid_sum_warp(pA, kGsMaxJ + 1 + wq);
+            if ((threadIdx.x & 31) == 0) {
+                const double gji = gams[j - 1] * gams[wq] * sum;            // G_ji = v_j . v_i
+                gs[j - 1][wq] = (float)gji;
+                if (blockIdx.x == 0) gram[(size_t)(j - 1) * ldg + wq] = gji;
+            }
         }
     }
     __syncthreads();
     // ---- forward substitution h_k = c_k - sum_{i<k} G_ki h_i (lane k-1 of warp 0).  The
     //      corrections are small next to c_k and are accumulated in FP32; h_k is FP64.
+    //      G is strictly lower triangular, so the sweeps h <- c - G h reach the solution
+    //      after at most j of them, and after a few when the basis is nearly orthogonal;
+    //      each sweep is one independent FMA chain per lane instead of j dependent shuffle
+    //      steps.  The sweeps stop once the FP32 corrections no longer change (the same
+    //      decision in every block); otherwise the sequential substitution finishes.
     if (threadIdx.x < 32) {
         const int l = threadIdx.x;
         const double r = l < j ? cs[l] : 0.0;
         const float rf = (float)r;
         float corr = 0.f;
-        for (int i = 0; i < j; ++i) {
-            const float hi = __shfl_sync(0xffffffffu, __fsub_rn(rf, corr), i);
-            if (l > i && l < j) corr = __fmaf_rn(gs[l][i], hi, corr);
+        bool done = false;
+        for (int sweep = 0; sweep < 4 && !done; ++sweep) {
+            hsm[l] = __fsub_rn(rf, corr);
+            __syncwarp();
+            float c2 = 0.f;
+            if (l < j)
+                for (int i = 0; i < l; ++i) c2 = __fmaf_rn(gs[l][i], hsm[i], c2);
+            __syncwarp();
+            done = __all_sync(0xffffffffu, c2 == corr);
+            corr = c2;
+        }
+        if (!done) {
+            corr = 0.f;
+            float gnext = l < j ? gs[l][0] : 0.f;   // the next G entry is read one step ahead
+            for (int i = 0; i < j; ++i) {
+                const float gcur = (l > i && l < j) ? gnext : 0.f;
+                gnext = (i + 1 < j && l < j) ? gs[l][i + 1] : 0.f;
+                const float hi = __shfl_sync(0xffffffffu, __fsub_rn(rf, corr), i);
+                corr = __fmaf_rn(gcur, hi, corr);
+            }
         }
         if (l < j) {
             const double h = r - (double)corr;
-            as[l] = (float)(h * ctrl->gam[l]);
+            as[l] = (float)(h * gams[l]);
             if (blockIdx.x == 0) H[l * ldh + (j - 1)] = h;
         }
     }
     __syncthreads();
-    // ---- sweep B1: w' = w - sum_k h_kj v_k;  sweep B2: W_k . w' and ||w'||^2
-    for (unsigned q = q0; q < NG; q += S) {
-        const bool full = 4u * q + 3u < N;
-        float4 x = ld4(w, q, full);
-        for (int k0 = 1; k0 <= j; k0 += 4) {
-            float4 v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                v[u] = k0 + u <= j ? ld4(W(k0 + u), q, full) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (k0 + u <= j) {
-                    const float a_ = -as[k0 + u - 1];
-                    x.x = __fmaf_rn(a_, v[u].x, x.x);
-                    x.y = __fmaf_rn(a_, v[u].y, x.y);
-                    x.z = __fmaf_rn(a_, v[u].z, x.z);
-                    x.w = __fmaf_rn(a_, v[u].w, x.w);
-                }
-        }
-        if (full) {
-            reinterpret_cast<float4 *>(w)[q] = x;
-        } else {
-            if (4u * q + 0u < N) w[4u * q + 0u] = x.x;
-            if (4u * q + 1u < N) w[4u * q + 1u] = x.y;
-            if (4u * q + 2u < N) w[4u * q + 2u] = x.z;
-        }
-    }
-    for (int k0 = 1; k0 <= j + 1; k0 += kGsChunk) {
-        const int nk = min(kGsChunk, j + 2 - k0);
+    // ---- round B: w' = w - sum_k h_kj v_k (eight columns per batch) and ||w'||^2
+    {
+        const int ncU = (j + 7) / 8;
         DotAcc<float> acc[kGsChunk];
-        for (unsigned q = q0; q < NG; q += S) {
+        for (unsigned q = q0, ri = 0; q < NG; q += S, ++ri) {
             const bool full = 4u * q + 3u < N;
-            const float4 wv = ld4(w, q, full);
+            float4 x = res ? wsm[ri * kArnThreads + threadIdx.x] : ld4(w, q, full);
+            for (int cB = 0; cB < ncU; ++cB) {
+                const int k0 = 1 + (down ? cB : ncU - 1 - cB) * 8;
+                float4 v[8];
 #pragma unroll
-            for (int h = 0; h < kGsChunk; h += 4) {
-                float4 v[4];
+                for (int u = 0; u < 8; ++u)
+                    v[u] = k0 + u <= j ? ld4(W(k0 + u), q, full) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    v[u] = h + u < nk ? (k0 + h + u <= j ? ld4(W(k0 + h + u), q, full) : wv)
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (h + u < nk) {
-                        acc[h + u].add(wv.x, v[u].x);
-                        acc[h + u].add(wv.y, v[u].y);
-                        acc[h + u].add(wv.z, v[u].z);
-                        acc[h + u].add(wv.w, v[u].w);
+                for (int u = 0; u < 8; ++u)
+                    if (k0 + u <= j) {
+                        const float a_ = -as[k0 + u - 1];
+                        x.x = __fmaf_rn(a_, v[u].x, x.x);
+                        x.y = __fmaf_rn(a_, v[u].y, x.y);
+                        x.z = __fmaf_rn(a_, v[u].z, x.z);
+                        x.w = __fmaf_rn(a_, v[u].w, x.w);
                     }
             }
+            if (full) {
+                reinterpret_cast<float4 *>(w)[q] = x;
+            } else {
+                if (4u * q + 0u < N) w[4u * q + 0u] = x.x;
+                if (4u * q + 1u < N) w[4u * q + 1u] = x.y;
+                if (4u * q + 2u < N) w[4u * q + 2u] = x.z;
+            }
+            // zero past N (partial groups hold zeros)
+            acc[0].add_value(__fmaf_rn(x.w, x.w, __fmaf_rn(x.z, x.z, __fmaf_rn(x.y, x.y, __fmul_rn(x.x, x.x)))));
         }
-        gs_block_sums(acc, nk, red, bout);
-        if (threadIdx.x < nk) pB[(size_t)(k0 - 1 + threadIdx.x) * G + blockIdx.x] = bout[threadIdx.x];
+        gs_block_sums(acc, 1, red, bout);
+        if (threadIdx.x == 0) pB[blockIdx.x] = bout[0];
     }
     gb.sync();
-    {
-        const int wq = threadIdx.x >> 5;
-        if (wq <= j) {
-            const double sum = gs_grid_sum_warp(pB, wq);
-            if ((threadIdx.x & 31) == 0) cs[wq] = sum;
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const double nrm2 = gs_grid_sum_warp(pB, 0);
+        if (threadIdx.x == 0) {
+            const double hn = sqrt(nrm2);                         // h_{j+1,j} (Fig. 2 line 9)
+            ctrl->hnext2 = nrm2;
+            H[j * ldh + (j - 1)] = hn;
+            ctrl->gam[j] = 1.0 / hn;
         }
-    }
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const double nrm2 = cs[j];
-        const double hn = sqrt(nrm2);                         // h_{j+1,j} (Fig. 2 line 9)
-        ctrl->hnext2 = nrm2;
-        H[j * ldh + (j - 1)] = hn;
-        ctrl->gam[j] = 1.0 / hn;
-        for (int k = 0; k < j; ++k)                           // G_{j+1,k} = v_{j+1} . v_k
-            gram[(size_t)j * ldg + k] = ctrl->gam[k] * cs[k] / hn;
     }
 }
 
@@ -883,9 +1017,9 @@ void launch_arnoldi_gmgs(const Launch &L, int blocks, const Geom &g, float *slot
                          int64_t ldv, const float *D, float *t, double *H, int ldh, int j,
                          float2 *gpart, double *gram, int ldg) {
     LaunchScope scope(L, CH_K_ARNOLDI);
-    {   // stages as the MGS form; j dots, j update fma and j + 1 dots (FP32, counted as flops)
+    {   // stages as the MGS form; j + (j - 1) dots, j update fma and the norm (FP32)
         const double N = (double)g.N, d = g.dim;
-        scope.work(((1.0 + 3.0 * d) + (1.0 + 3.0 * d) + 6.0 * j + 2.0) * N, (6.0 + 3.0 * j) * 4.0 * N);
+        scope.work(((1.0 + 3.0 * d) + (1.0 + 3.0 * d) + 6.0 * j + 2.0) * N, (6.0 + 2.0 * j) * 4.0 * N);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks, 1, 1);
