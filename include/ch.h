@@ -182,7 +182,8 @@ typedef enum {
     CH_K_LIM2,          /* stage 2 fused with the LIM update (Fig. 1 steps 6/10) */
     CH_K_ENERGY,        /* energy and mass */
     CH_K_ARM,           /* Krylov start: beta, tol_phi (Eq. tol_phi) */
-    CH_K_ARNOLDI,       /* a whole Arnoldi iteration (Fig. 2 lines 4-9) in one launch */
+    CH_K_ARNOLDI,       /* a whole Arnoldi iteration (Fig. 2 lines 4-9) in one launch
+                           (sequential passes; Gram-corrected on FP32 grids, j <= 31) */
     CH_K_COUNT
 } ch_kernel_class;
 
@@ -199,8 +200,9 @@ ch_status ch_timing_read(ch_grid *g, double *total_ms, int64_t *timed_launches,
 
 /* Algorithmic work of the launches timed since ch_timing_start: floating-point operations
  * (an FMA counts 2) and the bytes the method must move, as each launch computes them from
- * its sizes.  Reported by the classes CH_K_ARNOLDI (Arnoldi iteration j on N points:
- * (4 + 6d + 4j) N flops, (5 + j) N values moved), CH_K_RESID1 ((2 + 3d) N flops, 32 N
+ * its sizes.  Reported by the classes CH_K_ARNOLDI (Arnoldi iteration j on N points; FP64
+ * sequential passes: (4 + 6d + 4j) N flops, (5 + j) N values moved; FP32 Gram-corrected
+ * form: (4 + 6d + 6j) N flops, (6 + 2j) N values), CH_K_RESID1 ((2 + 3d) N flops, 32 N
  * bytes) and CH_K_LIM2 ((5 + 3d) N flops, 32 N bytes); 0 for the others.  Does not
  * synchronise; read it after ch_timing_read.                                            */
 ch_status ch_timing_work(ch_grid *g, double *flops, double *bytes);
