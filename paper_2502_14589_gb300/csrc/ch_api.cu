@@ -172,9 +172,11 @@ static void rhs(ch_grid *g, const double *y, double *out, int eyre, int mode,
 // basis precision VT.  The result y0 + V_j (beta u) is written to ynext (FP64); the run's
 // scalars are left in ctrl (not synchronised).
 // Krylov dimensions evaluated together by one projected-phi launch (Fig. 2 lines 10-14 for
-// j0..j0+3 from the same H).  Iterations past the j at exit are speculative work: their
-// A_hat products are not counted as matvecs and their basis columns are never combined.
-constexpr int kPhiBlock = 4;
+// j0..j0+7 from the same H, one cluster each).  Iterations past the j at exit are
+// speculative work: their A_hat products are not counted as matvecs and their basis
+// columns are never combined.  Eight per launch halves the phi launches of a run to m_max
+// = 30 against four, for at most four more speculative iterations when a run stops early.
+constexpr int kPhiBlock = 8;
 
 // Kernels of Arnoldi iterations j0..j1 (Fig. 2 lines 4-9, 21), the projected phi and residual
 // tests of those dimensions, and the copy of the device `active` flag to pinned memory.
