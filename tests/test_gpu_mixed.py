@@ -33,7 +33,9 @@ def host(t):
 @pytest.mark.parametrize("dim,n,eps,tau", [(2, (128, 128), 0.02, 2e-7), (2, (256, 256), 0.01, 2e-8),
                                            (3, (32, 32, 32), 0.03, 1e-6),
                                            (2, (1024, 1024), 0.01, 1e-8),     # resident FP32 iteration
-                                           (3, (144, 144, 144), 0.02, 1e-7)])  # streaming FP32 iteration
+                                           (3, (144, 144, 144), 0.02, 1e-7),  # streaming FP32 iteration
+                                           (2, (37, 53), 0.03, 1e-6),         # rows not a multiple of 4,
+                                           (3, (10, 9, 11), 0.05, 1e-5)])     # partial last group
 def test_mixed_krylov_step(ch, oracle, dim, n, eps, tau):
     y = inputs.initial_state(n, 3, -0.05, 0.05)
     og = oracle.Grid(dim, n, eps)
