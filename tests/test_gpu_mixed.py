@@ -85,3 +85,23 @@ def test_mixed_grid_lim_runs_fp64(ch, oracle):
     yo, po, lo, _ = oracle.lim_step(oracle.Grid(2, n, 0.05), y, 3e-6)
     assert p == po
     assert np.linalg.norm(yg - yo) / np.linalg.norm(yo) < 1e-12
+
+
+def test_mixed_krylov_beyond_31_dimensions(ch, oracle):
+    """A run that needs more than 31 Krylov dimensions (128^2, tau lambda_max ~ 100, m_max 40):
+    the FP32 basis uses the Gram-corrected iteration up to j = 31 and the sequential passes
+    after it, in the same run."""
+    n, eps, tau, tphi = (128, 128), 0.02, 1.5e-5, 1e-7
+    y = inputs.initial_state(n, 3, -0.05, 0.05)
+    og = oracle.Grid(2, n, eps)
+    lmax = oracle.lambda_max(og, y)
+    with ch.Grid(2, n, eps, ch.CH_MIXED, mmax_capacity=40) as G:
+        yn = torch.empty(G.N, dtype=torch.float64, device="cuda")
+        tu, st = ch.ch_phi_krylov(G.h, dev(y), tau, tphi, 40, 0, yn)
+        yg = host(yn)
+    print(f"mixed run with m_max 40: tau={tu:.3g} matvecs={st['matvecs']}")
+    assert st["matvecs"] > 32
+    rc, yo, _, _, _ = oracle.ee_step(og, y, tu, tol_phi_fixed=tphi, mmax=40)
+    assert rc == 0
+    assert np.linalg.norm(yg - yo) / np.linalg.norm(yo - y) < 50 * U32 * max(tu * lmax, 1.0)
+    assert abs(yg.mean() - y.mean()) < 1e-13
