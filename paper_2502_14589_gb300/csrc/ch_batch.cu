@@ -755,6 +755,10 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
         }
         b->offsets[i] = off;
         off += (N + 63) / 64 * 64;
+        if (off >= ((int64_t)1 << 31)) {   // checked per instance, before the sum can overflow
+            delete b;
+            return bfail(CH_EINVAL, "batch of more than 2^31 - 1 values (at instance %d)", i);
+        }
     }
     b->offsets[count] = off;
     b->Ntot = off;
