@@ -153,3 +153,37 @@ def test_energy_and_mass_closed_forms(oracle):
     grad = 0.5 * eps ** 2 * a ** 2 * (2 * np.sin(np.pi / n[0]) * n[0]) ** 2 * 0.5
     Fsum = np.mean(0.25 * (1 - y ** 2) ** 2)
     assert abs(oracle.energy(g, y) - (Fsum + grad)) < 1e-14
+
+
+@pytest.mark.parametrize("dim,n", [(2, (6, 6)), (2, (7, 5)), (3, (4, 5, 3))])
+def test_jacobian_spectrum_follows_propositions_1_and_2(oracle, dim, n):
+    """Sec. 3, Propositions 1 and 2, on the oracle's A_hat assembled column by column from its
+    Jacobian action: the eigenvalues are real and coincide with those of the symmetric
+    A^{1/2}(J + eps^2 A)A^{1/2} (A^{1/2} from the test's own dense Laplacian); A_hat has no
+    more negative (positive) eigenvalues than J + eps^2 A; with the Eyre term (Eq. A_g_cs)
+    every eigenvalue is nonnegative, so I + tau A_hat is nonsingular."""
+    eps = 0.1
+    y = inputs.initial_state(n, 21, -0.6, 0.6)
+    A = dense_A(n)
+    lam, Q = np.linalg.eigh(A)
+    sqrtA = (Q * np.sqrt(np.clip(lam, 0.0, None))) @ Q.T
+    N = y.size
+    for eyre in (False, True):
+        g = oracle.Grid(dim, n, eps, eyre=eyre)
+        M = np.column_stack([oracle.jacvec(g, y, np.eye(N)[:, k]) for k in range(N)])
+        B = np.diag(3 * y ** 2 - 1 + (1.0 if eyre else 0.0)) + eps ** 2 * A
+        ev = np.linalg.eigvals(M)
+        scale = np.abs(ev).max()
+        assert np.abs(ev.imag).max() < 1e-9 * scale
+        ev = np.sort(ev.real)
+        ev_sym = np.linalg.eigvalsh(sqrtA @ B @ sqrtA)
+        assert np.abs(ev - ev_sym).max() < 1e-9 * scale
+        eB = np.linalg.eigvalsh(B)
+        cut = 1e-9 * scale
+        assert (ev < -cut).sum() <= (eB < -cut).sum()
+        assert (ev > cut).sum() <= (eB > cut).sum()
+        if eyre:
+            assert ev.min() > -cut
+            assert np.linalg.eigvals(np.eye(N) + 1e-3 * M).real.min() >= 1.0 - 1e-9
+        else:
+            assert ev.min() < -cut       # this y makes J + eps^2 A indefinite: A_hat is too
