@@ -110,6 +110,35 @@ def test_phi_krylov_nonlinear_rt(ch, oracle, dim, n, tau, mmax):
     assert rel(host(yn), yo) < 1e-12
 
 
+@pytest.mark.parametrize("n,tau,precision", [((40, 52), 4e-4, "fp64"), ((64, 64), 1.5e-4, "fp64"),
+                                             ((64, 64), 3e-4, "fp64"), ((64, 64), 1.5e-4, "mixed")])
+def test_phi_krylov_beyond_64_dimensions(ch, oracle, n, tau, precision):
+    """The EE2(100) configuration of Sec. 5: m_max = 100 (Krylov runs ending at j = 65, 76 and
+    at m_max with the step trace), where each dimension's projected phi (n = j + 1 > 64) works
+    from global memory on one CTA.  FP64 is element by element; the mixed run (FP32 basis) is
+    held to its FP32 bound against the oracle run of the step it took."""
+    eps, tol_phi, mmax = 0.05, 1e-8, 100
+    y = inputs.initial_state(n, 6, -0.05, 0.05)
+    og = oracle.Grid(2, n, eps)
+    prec = ch.CH_FP64 if precision == "fp64" else ch.CH_MIXED
+    with ch.Grid(2, n, eps, prec, mmax_capacity=mmax) as G:
+        yn = torch.empty(G.N, dtype=torch.float64, device="cuda")
+        tu, st = ch.ch_phi_krylov(G.h, dev(y), tau, tol_phi, mmax, 0, yn)
+        yg = host(yn)
+    rc, yo, to, jo, sto = oracle.ee_step(og, y, tu if precision == "mixed" else tau,
+                                         tol_phi_fixed=tol_phi, mmax=mmax, linear_restart=False)
+    assert rc == 0
+    assert st["matvecs"] > 65
+    if precision == "fp64":
+        assert tu == pytest.approx(to, rel=1e-12, abs=0)
+        assert st["matvecs"] == sto["matvecs"]
+        assert rel(yg, yo) < 1e-12
+    else:
+        lmax = oracle.lambda_max(og, y)
+        assert np.linalg.norm(yg - yo) / np.linalg.norm(yo - y) < 50 * 2.0 ** -24 * max(tu * lmax, 1.0)
+        assert abs(yg.mean() - y.mean()) < 1e-13
+
+
 @pytest.mark.parametrize("dim,n,tau,mmax", [(2, (64, 64), 1e-6, 30), (2, (40, 44), 2e-5, 5),
                                             (3, (10, 9, 11), 3e-5, 8)])
 def test_phi_krylov_linear_restart(ch, oracle, dim, n, tau, mmax):
