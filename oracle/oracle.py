@@ -72,10 +72,12 @@ _D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 
 
 def lib():
+    """The oracle library.  CH_ORACLE_LIB names another build of ch_oracle.c to load instead
+    (the mutation test compiles copies with planted mistakes and runs the pins on them)."""
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            L = C.CDLL(os.environ.get("CH_ORACLE_LIB") or build())
             G = C.POINTER(OrGrid)
             sig = {
                 "or_apply_A": (None, [G, _D, _D]),

@@ -107,9 +107,15 @@ def test_krylov_shrinks_step_and_meets_tolerance(oracle):
     exact = y + scipy.linalg.expm(aug)[:N, N]
     beta = np.linalg.norm(g - M @ y)
     assert np.linalg.norm(out - exact) < 100 * tol * beta * taken
-    # the next bisection point beyond `taken` must fail the test (maximality, to 2^-12)
-    rc2, _, taken2, _ = oracle.krylov_dense(M, g, y, taken * (1 + 2 ** -10), tol, mmax)
-    assert taken2 < taken * (1 + 2 ** -10)
+    # Maximality at the trace's resolution: halving from tau0 stops at the first admissible
+    # lo0 = tau0 / 2^k, and 12 bisections of [lo0, 2 lo0] leave an inadmissible end within
+    # lo0 / 2^12 <= taken / 2^12 of the step; a run started just beyond it must be cut.
+    for tau0_, tol_, mmax_ in [(tau0, tol, mmax), (3e-3, 1e-7, 5), (1e-2, 1e-6, 3), (5e-3, 1e-8, 6)]:
+        rc, _, taken, j = oracle.krylov_dense(M, g, y, tau0_, tol_, mmax_)
+        assert rc == 0 and j == mmax_ and 0 < taken < tau0_
+        start = taken * (1 + 2.0 ** -12)
+        rc2, _, taken2, _ = oracle.krylov_dense(M, g, y, start, tol_, mmax_)
+        assert rc2 == 0 and taken2 < start
 
 
 def test_grid_ee_step_linear_restart_matches_exact(oracle):

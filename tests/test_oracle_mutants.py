@@ -1,0 +1,87 @@
+"""Mutation check of the oracle's pins: each case plants one plausible mistake (a sign, an
+index, a dropped term or factor, a transposed operand, a wrong coefficient) in a copy of
+ch_oracle.c, builds it, and runs the oracle's pin tests against that build through
+CH_ORACLE_LIB.  Every mutant must make at least one pin fail; the unmodified copy must
+pass them all.  The planted mistakes exist only in temporary copies on the CPU."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ch_oracle.c")
+PINS = [os.path.join(ROOT, "tests", f) for f in
+        ("test_oracle_operators.py", "test_oracle_krylov.py", "test_oracle_lim.py",
+         "test_oracle_drivers.py")]
+
+# (name, original text, planted text): the original must occur exactly once in ch_oracle.c
+MUTANTS = [
+    ("A: sign of a neighbour", "- v[shift(g, i, a, +1)] - v[shift(g, i, a, -1)]",
+     "- v[shift(g, i, a, +1)] + v[shift(g, i, a, -1)]"),
+    ("A: neighbour offset", "- v[shift(g, i, a, -1)]);", "- v[shift(g, i, a, -2)]);"),
+    ("F': dropped linear term", "return c * (c * c - 1.0);", "return c * c * c;"),
+    ("J: sign of the identity", "return 3.0 * y * y - 1.0;", "return 3.0 * y * y + 1.0;"),
+    ("f: eps instead of eps^2", "mu[i] = Fp(y[i]) + g->eps * g->eps * Ay[i];",
+     "mu[i] = Fp(y[i]) + g->eps * Ay[i];"),
+    ("g_hat: Eyre term dropped", "if (g->eyre) t[i] += yn[i];", "if (g->eyre) t[i] += 0.0;"),
+    ("A_hat: Eyre term sign", "if (g->eyre) t[i] += v[i];", "if (g->eyre) t[i] -= v[i];"),
+    ("lambda_max: |d_j| in the column", "dj * Ae[k].val", "fabs(dj) * Ae[k].val"),
+    ("Eq. p: sqrt dropped", "atan(sqrt(tau * lambda_max))", "atan(tau * lambda_max)"),
+    ("Fig. 1: sign of beta_m in a_m", "(z1 - beta[m - 1])", "(z1 + beta[m - 1])"),
+    ("Fig. 1: y^n for y^(prev)", "tau * am * prev[i] +", "tau * am * yn[i] +"),
+    ("Fig. 1: second sweep from m = 1", "(sweep == 0 ? 0 : 1)", "(sweep == 0 ? 0 : 0)"),
+    ("Pade: coefficient denominator", "((double)(2 * m - k + 1) * k)", "((double)(2 * m - k) * k)"),
+    ("expm: one squaring short", "for (int k = 0; k < sq; ++k) { mat_mul",
+     "for (int k = 1; k < sq; ++k) { mat_mul"),
+    ("phi: augmented column not scaled", "M[0 * n + j] = s;", "M[0 * n + j] = 1.0;"),
+    ("phi: transposed H", "M[r * n + c] = -s * H[r * ldh + c];", "M[r * n + c] = -s * H[c * ldh + r];"),
+    ("Fig. 2: v_1 sign", "V[i] = g[i] - w[i];", "V[i] = g[i] + w[i];"),
+    ("Fig. 2: residual entry index", "return hnext * fabs(u[j - 1]);", "return hnext * fabs(u[0]);"),
+    ("Fig. 2: subdiagonal not stored", "H[j * ldh + (j - 1)] = hnext;", "H[j * ldh + (j - 1)] = 0.0;"),
+    ("Fig. 2: beta dropped in the combine", "* (beta * u[c]);", "* (u[c]);"),
+    ("Fig. 2: trace quarters instead of halving", "hi = lo; lo = 0.5 * lo;", "hi = lo; lo = 0.25 * lo;"),
+    ("Eq. tol_phi: factor 10 dropped", "norm_ghat / (10.0 * beta)", "norm_ghat / beta"),
+    ("Eq. LIMest: full step in the corrector", "ypc[i] = yn[i] - 0.5 * tau * Asum[i];",
+     "ypc[i] = yn[i] - tau * Asum[i];"),
+    ("Eq. EEdt: square root dropped", "sqrt(prm->tol / est) * taken", "(prm->tol / est) * taken"),
+    ("Eq. LIMdt: square root added", "? (prm->tol / est) * taken : taken;",
+     "? sqrt(prm->tol / est) * taken : taken;"),
+    ("energy: gradient term doubled", "0.5 * g->eps * g->eps * sG", "g->eps * g->eps * sG"),
+    ("mass: cell volume dropped", "return vol * s;", "return s;"),
+]
+
+
+def _build(tmp_path, name, text):
+    c = tmp_path / f"{name}.c"
+    so = tmp_path / f"{name}.so"
+    c.write_text(text)
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
+                           "-ffp-contract=off", "-o", str(so), str(c), "-lm"])
+    return str(so)
+
+
+def _run_pins(so, first_failure):
+    env = dict(os.environ, CH_ORACLE_LIB=so)
+    args = [sys.executable, "-m", "pytest", "-q", "-m", "not gpu", "-p", "no:cacheprovider"]
+    if first_failure:
+        args.append("-x")
+    r = subprocess.run(args + PINS, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def source():
+    return open(SRC).read()
+
+
+def test_unmodified_copy_passes_every_pin(source, tmp_path):
+    rc, out = _run_pins(_build(tmp_path, "control", source), False)
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name,orig,planted", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_every_planted_mistake_fails_a_pin(source, tmp_path, name, orig, planted):
+    assert source.count(orig) == 1, f"mutation site not unique or gone: {orig!r}"
+    rc, out = _run_pins(_build(tmp_path, "mutant", source.replace(orig, planted)), True)
+    assert rc == 1, f"{name}: no pin failed (pytest exit {rc})\n{out}"
