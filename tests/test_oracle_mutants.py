@@ -6,6 +6,7 @@ pass them all.  The planted mistakes exist only in temporary copies on the CPU."
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -52,13 +53,14 @@ MUTANTS = [
 ]
 
 
-def _build(tmp_path, name, text):
-    c = tmp_path / f"{name}.c"
-    so = tmp_path / f"{name}.so"
-    c.write_text(text)
+def _build(dirpath, name, text):
+    c = os.path.join(dirpath, f"{name}.c")
+    so = os.path.join(dirpath, f"{name}.so")
+    with open(c, "w") as fh:
+        fh.write(text)
     subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
-                           "-ffp-contract=off", "-o", str(so), str(c), "-lm"])
-    return str(so)
+                           "-ffp-contract=off", "-o", so, c, "-lm"])
+    return so
 
 
 def _run_pins(so, first_failure):
@@ -75,13 +77,30 @@ def source():
     return open(SRC).read()
 
 
-def test_unmodified_copy_passes_every_pin(source, tmp_path):
-    rc, out = _run_pins(_build(tmp_path, "control", source), False)
+@pytest.fixture(scope="module")
+def outcomes(source, tmp_path_factory):
+    """Build every copy and run the pins on each, a few copies at a time."""
+    d = str(tmp_path_factory.mktemp("mutants"))
+    jobs = [("control", source, False)]
+    jobs += [(name, source.replace(orig, planted), True) for name, orig, planted in MUTANTS
+             if source.count(orig) == 1]
+
+    def run(k):
+        key, text, first = jobs[k]
+        return key, _run_pins(_build(d, f"copy{k}", text), first)
+
+    workers = max(1, min(6, (os.cpu_count() or 2) // 2))
+    with ThreadPoolExecutor(workers) as ex:
+        return dict(ex.map(run, range(len(jobs))))
+
+
+def test_unmodified_copy_passes_every_pin(outcomes):
+    rc, out = outcomes["control"]
     assert rc == 0, out
 
 
 @pytest.mark.parametrize("name,orig,planted", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_every_planted_mistake_fails_a_pin(source, tmp_path, name, orig, planted):
+def test_every_planted_mistake_fails_a_pin(source, outcomes, name, orig, planted):
     assert source.count(orig) == 1, f"mutation site not unique or gone: {orig!r}"
-    rc, out = _run_pins(_build(tmp_path, "mutant", source.replace(orig, planted)), True)
+    rc, out = outcomes[name]
     assert rc == 1, f"{name}: no pin failed (pytest exit {rc})\n{out}"
