@@ -245,8 +245,9 @@ def main():
     dist = None
     if world > 1:
         import torch.distributed as dist
-        import torch
-        torch.cuda.set_device(local_rank)
+        if args.impl == "gb300":                 # the reference arm runs on the host only
+            import torch
+            torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
     if args.impl == "reference":
         run_reference(args, rank, world)
