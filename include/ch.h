@@ -107,18 +107,22 @@ ch_status ch_estimate(ch_grid *g, const double *y0, const double *y1, double tau
  * tau0, tolerance tol_phi (> 0) and dimension mmax.  linear_restart = 0: the run may cut
  * tau (residual-time step choice, Eq. phi_stop) and *tau_used returns the step taken;
  * linear_restart = 1: linear residual-time restarting covers all of tau0 (constant-step
- * use, end of Sec. 4.1).  y_next may not alias y_n.  `stats` (optional) is incremented.  */
+ * use, end of Sec. 4.1).  y_next may not alias y_n.  `stats` (optional) is incremented.
+ * CH_EINVAL when tau0 is not finite and > 0, tol_phi <= 0 or mmax is outside [1, capacity]. */
 ch_status ch_phi_krylov(ch_grid *g, const double *y_n, double tau0, double tol_phi, int mmax,
                         int linear_restart, int eyre, double *y_next, double *tau_used,
                         ch_stats *stats);
 
 /* One EE2 step (Sec. 4, Eqs. IVPlin, EE2) with the Krylov tolerance of prm (Eq. tol_phi
  * when prm->tol_phi <= 0), linear restarting when prm->adaptive == 0, and the error
- * estimate of Eq. (LIMest) for the step actually taken.  Synchronises.                    */
+ * estimate of Eq. (LIMest) for the step actually taken.  Synchronises.  CH_EINVAL when tau
+ * is not finite and > 0 or prm is invalid.                                                */
 ch_status ch_ee_step(ch_grid *g, const double *y_n, double tau, const ch_params *prm,
                      double *y_next, double *tau_used, double *est);
 
-/* One LIM step (Sec. 3.1, Fig. 1).  Returns the Chebyshev order p and lambda_max.        */
+/* One LIM step (Sec. 3.1, Fig. 1).  Returns the Chebyshev order p and lambda_max.
+ * CH_EINVAL when tau is not finite and > 0 or p of Eq. (p) would exceed 10^6;
+ * CH_ENONFINITE when lambda_max is not finite (non-finite y_n).                          */
 ch_status ch_lim_step(ch_grid *g, const double *y_n, double tau, int eyre, double *y_next,
                       int *p_used, double *lambda_max);
 

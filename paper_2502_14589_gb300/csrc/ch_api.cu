@@ -153,10 +153,12 @@ static double lambda_from_minmax(const Geom &G, double y2min, double y2max, int 
     return std::max(col_abs_sum(G, dmin), col_abs_sum(G, dmax));
 }
 
-// Eq. (p)
+// Eq. (p); -1 when tau * lambda_max is not finite or p would exceed 10^6 (checked on the
+// double, before the conversion to int)
 static int cheb_order(double tau, double lmax) {
     const double pi = 3.14159265358979323846;
-    return (int)ceil((pi / 4.0) / (pi / 2.0 - atan(sqrt(tau * lmax))));
+    const double p = ceil((pi / 4.0) / (pi / 2.0 - atan(sqrt(tau * lmax))));
+    return (p >= 1.0 && p <= 1e6) ? (int)p : -1;
 }
 
 // f = rhs(y) into out; mode bits of k_rhs2 (1: ||f||^2, 2: ||g_hat||^2, 4: est sums,
@@ -418,7 +420,9 @@ static ch_status lim_step_impl(ch_grid *g, const double *yn, double tau, double 
     const Launch &L = g->L;
     const double pi = 3.14159265358979323846;
     const int p = cheb_order(tau, lmax);                                   // step 1
-    if (p < 1 || p > 1000000) return fail(CH_EINVAL, "Chebyshev order %d out of range", p);
+    if (p < 1)
+        return fail(isfinite(lmax) ? CH_EINVAL : CH_ENONFINITE,
+                    "Chebyshev order for tau * lambda_max = %g out of range", tau * lmax);
     std::vector<double> beta(p), a(p);
     for (int i = 1; i <= p; ++i) beta[i - 1] = cos(pi * (2.0 * i - 1.0) / (2.0 * p));   // 2
     const double z1 = beta[0];                                             // step 3
@@ -778,7 +782,8 @@ ch_status ch_phi_krylov(ch_grid *g, const double *y_n, double tau0, double tol_p
     if (!g || !y_n || !y_next) return fail(CH_EINVAL, "null argument");
     if (y_n == y_next) return fail(CH_EINVAL, "y_next may not alias y_n");
     if (mmax < 1 || mmax > g->mmax_cap) return fail(CH_EINVAL, "mmax outside [1, capacity]");
-    if (!(tau0 > 0.0) || !(tol_phi > 0.0)) return fail(CH_EINVAL, "tau0 and tol_phi must be > 0");
+    if (!(tau0 > 0.0) || !(tol_phi > 0.0) || !isfinite(tau0))
+        return fail(CH_EINVAL, "tau0 must be finite and > 0, tol_phi > 0");
     rhs(g, y_n, g->F[0], eyre, 1);
     EEOut o;
     CH_TRY(ee_step_impl(g, y_n, 0, tau0, tol_phi, 0.0, mmax, linear_restart, eyre, y_next, 0, &o));
@@ -812,6 +817,7 @@ ch_status ch_ee_step(ch_grid *g, const double *y_n, double tau, const ch_params 
                      double *y_next, double *tau_used, double *est) {
     if (!g || !y_n || !y_next) return fail(CH_EINVAL, "null argument");
     if (y_n == y_next) return fail(CH_EINVAL, "y_next may not alias y_n");
+    if (!(tau > 0.0) || !isfinite(tau)) return fail(CH_EINVAL, "tau must be finite and > 0");
     CH_TRY(check_params(g, prm));
     const int use_ghat = !(prm->tol_phi > 0.0);
     rhs(g, y_n, g->F[0], prm->eyre, 1 | (use_ghat ? 2 : 0));
@@ -827,7 +833,7 @@ ch_status ch_lim_step(ch_grid *g, const double *y_n, double tau, int eyre, doubl
                       int *p_used, double *lambda_max) {
     if (!g || !y_n || !y_next) return fail(CH_EINVAL, "null argument");
     if (y_n == y_next) return fail(CH_EINVAL, "y_next may not alias y_n");
-    if (!(tau > 0.0)) return fail(CH_EINVAL, "tau must be > 0");
+    if (!(tau > 0.0) || !isfinite(tau)) return fail(CH_EINVAL, "tau must be finite and > 0");
     double lmax;
     CH_TRY(ch_lambda_max(g, y_n, eyre, &lmax));
     int p = 0;

@@ -253,6 +253,27 @@ def test_errors_are_reported(ch):
         assert st["t"] == 1e-6
 
 
+def test_step_sizes_are_validated(ch):
+    """Step sizes that are zero, negative, infinite or NaN are refused before any work, and a
+    LIM step from a non-finite state reports the non-finite lambda_max."""
+    with ch.Grid(2, (16, 16), 0.05) as G:
+        y = dev(inputs.initial_state((16, 16), 0))
+        yn = torch.empty_like(y)
+        prm = ch.make_params("ee2", True, 1e-5, 1e-7, 1e-6)
+        for tau in (0.0, -1e-6, float("inf"), float("nan")):
+            for call in (lambda: ch.ch_lim_step(G.h, y, tau, yn),
+                         lambda: ch.ch_ee_step(G.h, y, tau, prm, yn),
+                         lambda: ch.ch_phi_krylov(G.h, y, tau, 1e-8, 30, 0, yn)):
+                with pytest.raises(ch.CHError) as e:
+                    call()
+                assert e.value.status == ch.CH_EINVAL
+        with pytest.raises(ch.CHError) as e:
+            ch.ch_lim_step(G.h, dev(np.full(256, np.nan)), 1e-6, yn)
+        assert e.value.status == ch.CH_ENONFINITE
+        p, _ = ch.ch_lim_step(G.h, y, 1e-6, yn)       # the grid stays usable
+        assert p >= 1
+
+
 @pytest.mark.parametrize("scheme", ["ee2", "lim"])
 def test_checkpoint_resume_is_bit_identical(ch, scheme):
     """Stop after k steps (max_steps), read (t, tau_next), resume: same bits as one run."""
