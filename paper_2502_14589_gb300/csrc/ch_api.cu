@@ -855,7 +855,7 @@ ch_status ch_set_record_capacity(ch_grid *g, int64_t capacity) {
 ch_status ch_get_records(ch_grid *g, int64_t max, double *tau, int *jexit, int *restarts,
                          int *shrunk, int *p, double *est, int64_t *count) {
     if (!g) return fail(CH_EINVAL, "null grid");
-    const int64_t n = std::min<int64_t>(max, (int64_t)g->rec.size());
+    const int64_t n = std::max<int64_t>(0, std::min<int64_t>(max, (int64_t)g->rec.size()));
     for (int64_t k = 0; k < n; ++k) {
         const StepRecord &r = g->rec[(size_t)k];
         if (tau) tau[k] = r.tau;

@@ -868,8 +868,9 @@ ch_status ch_integrate_batch(ch_batch *b, const ch_params *prm, double *y, ch_st
     if (prm->scheme != CH_EE2 || !prm->adaptive)
         return bfail(CH_EINVAL, "the batch integrator runs adaptive EE2 (Fig. 4)");
     if (prm->eyre) return bfail(CH_EINVAL, "the batch integrator has no Eyre splitting");
-    if (!(prm->T > 0.0) || !(prm->tau0 > 0.0) || !(prm->tol > 0.0))
-        return bfail(CH_EINVAL, "T, tau0 and tol must be > 0");
+    if (!(prm->T > 0.0) || !(prm->tau0 > 0.0) || !(prm->tol > 0.0) || !isfinite(prm->T) ||
+        !isfinite(prm->tau0))
+        return bfail(CH_EINVAL, "T and tau0 must be finite and > 0, tol > 0");
     if (prm->mmax < 1 || prm->mmax > b->mmax_cap) return bfail(CH_EINVAL, "mmax outside [1, capacity]");
     if (prm->max_steps < 1) return bfail(CH_EINVAL, "max_steps must be >= 1");
     return b->precision == CH_MIXED ? integrate_b<float>(b, prm, y, stats)

@@ -81,3 +81,28 @@ def test_batch_3d_and_stationary_instance(ch, oracle):
         yo, sto = oracle_run(oracle, 3, (sides[i],) * 3, eps[i], y0s[i], T)
         assert st[i]["steps"] == sto["steps"]
         assert np.linalg.norm(ys[i] - yo) / np.linalg.norm(yo) < 1e-10
+
+
+def test_batch_arguments_are_validated(ch):
+    """Invalid run parameters are refused before any work, and the batch stays usable."""
+    h = ch.ch_create_batch(2, [16, 24], [0.05, 0.04], ch.CH_FP64, 30)
+    try:
+        offs, _ = ch.ch_batch_layout(h, 2)
+        y = torch.zeros(offs[-1], dtype=torch.float64, device="cuda")
+        for i, s in enumerate((16, 24)):
+            y[offs[i]:offs[i] + s * s] = torch.from_numpy(inputs.initial_state((s, s), 40 + i)).cuda()
+        bad = [ch.make_params("ee2", True, float("inf"), 1e-7, 1e-5),
+               ch.make_params("ee2", True, 1e-5, float("nan"), 1e-5),
+               ch.make_params("ee2", True, 1e-5, float("inf"), 1e-5),
+               ch.make_params("ee2", True, 1e-5, 1e-7, 0.0),
+               ch.make_params("ee2", True, 1e-5, 1e-7, 1e-5, mmax=31),
+               ch.make_params("lim", True, 1e-5, 1e-7, 1e-5),
+               ch.make_params("ee2", False, 1e-5, 1e-7, 1e-5)]
+        for prm in bad:
+            with pytest.raises(ch.CHError) as e:
+                ch.ch_integrate_batch(h, prm, y, 2)
+            assert e.value.status == ch.CH_EINVAL
+        st = ch.ch_integrate_batch(h, ch.make_params("ee2", True, 2e-6, 1e-7, 1e-5), y, 2)
+        assert all(s["t"] == 2e-6 for s in st)
+    finally:
+        ch.ch_destroy_batch(h)
