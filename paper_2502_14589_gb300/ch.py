@@ -118,6 +118,29 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+# Points a vector argument of each live grid or batch handle must hold, and the CUDA
+# device the handle's workspace lives on.  The C functions cannot check the length or the
+# device of a caller's buffer, so the binding does before passing the pointer on.
+_EXTENT = {}
+
+
+def _register(h, points):
+    import torch
+    _EXTENT[h.value] = (int(points), torch.cuda.current_device())
+
+
+def _vec(h, t):
+    p = _ptr(t)
+    ext = _EXTENT.get(getattr(h, "value", h))
+    if t is not None and ext is not None:
+        points, device = ext
+        if t.numel() < points:
+            raise ValueError(f"vector of {t.numel()} values; this handle needs {points}")
+        if t.device.index != device:
+            raise ValueError(f"vector on cuda:{t.device.index}; this handle lives on cuda:{device}")
+    return p
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -131,41 +154,43 @@ def ch_create_grid(dim, n, eps, precision=CH_FP64, mmax_capacity=30, stream=None
     arr = (C.c_int64 * 3)(*nn)
     h = C.c_void_p()
     _check(load().ch_create_grid(dim, arr, eps, precision, mmax_capacity, _stream(stream), C.byref(h)))
+    _register(h, nn[0] * nn[1] * nn[2])
     return h
 
 
 def ch_destroy_grid(h):
+    _EXTENT.pop(getattr(h, "value", h), None)
     _check(load().ch_destroy_grid(h))
 
 
 def ch_rhs(h, y, f, eyre=0, want_norms=False):
     nf, ng = C.c_double(), C.c_double()
-    _check(load().ch_rhs(h, _ptr(y), _ptr(f), int(eyre), C.byref(nf) if want_norms else None,
+    _check(load().ch_rhs(h, _vec(h, y), _vec(h, f), int(eyre), C.byref(nf) if want_norms else None,
                          C.byref(ng) if want_norms else None))
     return (nf.value, ng.value) if want_norms else None
 
 
 def ch_jacvec(h, y_lin, v, w, eyre=0):
-    _check(load().ch_jacvec(h, _ptr(y_lin), _ptr(v), _ptr(w), int(eyre)))
+    _check(load().ch_jacvec(h, _vec(h, y_lin), _vec(h, v), _vec(h, w), int(eyre)))
 
 
 def ch_lambda_max(h, y, eyre=0):
     out = C.c_double()
-    _check(load().ch_lambda_max(h, _ptr(y), int(eyre), C.byref(out)))
+    _check(load().ch_lambda_max(h, _vec(h, y), int(eyre), C.byref(out)))
     return out.value
 
 
 def ch_estimate(h, y0, y1, tau):
     out = C.c_double()
-    _check(load().ch_estimate(h, _ptr(y0), _ptr(y1), tau, C.byref(out)))
+    _check(load().ch_estimate(h, _vec(h, y0), _vec(h, y1), tau, C.byref(out)))
     return out.value
 
 
 def ch_phi_krylov(h, y_n, tau0, tol_phi, mmax, linear_restart, y_next, eyre=0):
     tu = C.c_double()
     st = ch_stats()
-    _check(load().ch_phi_krylov(h, _ptr(y_n), tau0, tol_phi, mmax, int(linear_restart), int(eyre),
-                                _ptr(y_next), C.byref(tu), C.byref(st)))
+    _check(load().ch_phi_krylov(h, _vec(h, y_n), tau0, tol_phi, mmax, int(linear_restart), int(eyre),
+                                _vec(h, y_next), C.byref(tu), C.byref(st)))
     return tu.value, st.as_dict()
 
 
@@ -177,19 +202,19 @@ def make_params(scheme="ee2", adaptive=True, T=1e-3, tau0=1e-7, tol=1e-6, mmax=3
 
 def ch_ee_step(h, y_n, tau, prm, y_next):
     tu, est = C.c_double(), C.c_double()
-    _check(load().ch_ee_step(h, _ptr(y_n), tau, C.byref(prm), _ptr(y_next), C.byref(tu), C.byref(est)))
+    _check(load().ch_ee_step(h, _vec(h, y_n), tau, C.byref(prm), _vec(h, y_next), C.byref(tu), C.byref(est)))
     return tu.value, est.value
 
 
 def ch_lim_step(h, y_n, tau, y_next, eyre=0):
     p, lm = C.c_int(), C.c_double()
-    _check(load().ch_lim_step(h, _ptr(y_n), tau, int(eyre), _ptr(y_next), C.byref(p), C.byref(lm)))
+    _check(load().ch_lim_step(h, _vec(h, y_n), tau, int(eyre), _vec(h, y_next), C.byref(p), C.byref(lm)))
     return p.value, lm.value
 
 
 def ch_integrate(h, prm, y):
     st = ch_stats()
-    _check(load().ch_integrate(h, C.byref(prm), _ptr(y), C.byref(st)))
+    _check(load().ch_integrate(h, C.byref(prm), _vec(h, y), C.byref(st)))
     return st.as_dict()
 
 
@@ -222,7 +247,7 @@ def ch_set_state(h, t, tau):
 
 def ch_energy_mass(h, y):
     e, m = C.c_double(), C.c_double()
-    _check(load().ch_energy_mass(h, _ptr(y), C.byref(e), C.byref(m)))
+    _check(load().ch_energy_mass(h, _vec(h, y), C.byref(e), C.byref(m)))
     return e.value, m.value
 
 
@@ -298,10 +323,12 @@ def ch_create_batch(dim, sizes, eps, precision=CH_FP64, mmax_capacity=30, stream
     ep = (C.c_double * count)(*[float(e) for e in eps])
     h = C.c_void_p()
     _check(load().ch_create_batch(dim, count, arr, ep, precision, mmax_capacity, _stream(stream), C.byref(h)))
+    _register(h, ch_batch_layout(h, count)[0][count])
     return h
 
 
 def ch_destroy_batch(h):
+    _EXTENT.pop(getattr(h, "value", h), None)
     _check(load().ch_destroy_batch(h))
 
 
@@ -314,7 +341,7 @@ def ch_batch_layout(h, count):
 
 def ch_integrate_batch(h, prm, y, count):
     st = (ch_stats * count)()
-    _check(load().ch_integrate_batch(h, C.byref(prm), _ptr(y), st))
+    _check(load().ch_integrate_batch(h, C.byref(prm), _vec(h, y), st))
     return [s.as_dict() for s in st]
 
 
@@ -326,4 +353,8 @@ def ch_energy_mass_noalloc(dim, n, eps, y, out, stream=None):
     """Energy and mass of y into the device tensor out[0:2] without any allocation (queued on
     the stream, not synchronised); see include/ch.h for whom this entry point is for."""
     nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    if y is not None and y.numel() < nn[0] * nn[1] * nn[2]:
+        raise ValueError(f"vector of {y.numel()} values; the grid has {nn[0] * nn[1] * nn[2]} points")
+    if out is not None and out.numel() < 2:
+        raise ValueError("out must hold 2 values")
     _check(load().ch_energy_mass_noalloc(dim, nn, eps, _ptr(y), _ptr(out), _stream(stream)))

@@ -253,6 +253,34 @@ def test_errors_are_reported(ch):
         assert st["t"] == 1e-6
 
 
+def test_binding_checks_vector_lengths(ch):
+    """The C functions cannot see the length of a caller's buffer; the binding refuses a
+    vector shorter than the grid (or the batch layout) before any launch."""
+    z = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")
+    with ch.Grid(2, (16, 16), 0.05) as G:
+        y = dev(inputs.initial_state((16, 16), 0))
+        with pytest.raises(ValueError):
+            ch.ch_rhs(G.h, z(255), z(256))
+        with pytest.raises(ValueError):
+            ch.ch_jacvec(G.h, y, y, z(100))
+        with pytest.raises(ValueError):
+            ch.ch_integrate(G.h, ch.make_params("lim", True, 1e-6, 1e-8, 1e-5), z(200))
+        f = z(300)                                  # longer buffers are fine
+        ch.ch_rhs(G.h, y, f)
+        ref = z(256)
+        ch.ch_rhs(G.h, y, ref)
+        assert torch.equal(f[:256], ref)
+    h = ch.ch_create_batch(2, [16, 24], [0.05, 0.04], ch.CH_FP64, 30)
+    try:
+        offs, _ = ch.ch_batch_layout(h, 2)
+        with pytest.raises(ValueError):
+            ch.ch_integrate_batch(h, ch.make_params("ee2", True, 1e-6, 1e-7, 1e-5), z(offs[-1] - 1), 2)
+    finally:
+        ch.ch_destroy_batch(h)
+    with pytest.raises(ValueError):
+        ch.ch_energy_mass_noalloc(2, (16, 16), 0.05, z(255), z(2))
+
+
 def test_step_sizes_are_validated(ch):
     """Step sizes that are zero, negative, infinite or NaN are refused before any work, and a
     LIM step from a non-finite state reports the non-finite lambda_max."""
