@@ -11,11 +11,15 @@
  *
  * Every routine follows one passage of the paper and says which.  Loops are written out
  * in the order the paper states the algorithm, with no blocking or fusion, so a reader
- * can check them against the paper by eye.  The spatial discretisation is the periodic
- * second-order finite-difference Laplacian on the unit square / cube, h_a = 1/n_a.
+ * can check them against the paper by eye.  The spatial discretisation is the second-order
+ * finite-difference Laplacian on the unit square / cube, h_a = 1/n_a, with periodic
+ * boundaries or with the paper's homogeneous Neumann conditions of Eq. (CH) on cell-centred
+ * nodes (Sec. 5.1: x_i = (i - 1/2) h), where a neighbour beyond the boundary is the mirror
+ * image of the point inside it.
  *
  * Readings of points where the paper is silent (listed in the design doc as well):
- *  - periodic boundary conditions instead of the paper's Neumann ones;
+ *  - periodic boundary conditions for the benchmark workloads; the paper's Neumann
+ *    conditions are the other choice of or_grid.bc;
  *  - "trace resnorm for s in [0,tau0]" (Fig. 2, RT algorithm) = halve s from the upper
  *    end until the residual test passes, then bisect a fixed number of times keeping
  *    the admissible end;
@@ -37,6 +41,7 @@ typedef struct {
     long n[3];      /* points per axis; n[2] == 1 when dim == 2 */
     double eps;     /* epsilon of the IVP (Sec. 2, Eq. IVP) */
     int eyre;       /* 0: A_hat, g_hat of Eq. (A_g); 1: Eyre splitting, Eq. (A_g_cs) */
+    int bc;         /* 0: periodic; 1: homogeneous Neumann (Eq. CH), cell-centred nodes */
 } or_grid;
 
 typedef struct {            /* counters of work, as the paper counts it (Sec. 5.1) */
@@ -58,19 +63,27 @@ static double or_s(const or_grid *g, int a) { /* 1/h_a^2 with h_a = 1/n_a */
 
 static long wrap(long i, long n) { long r = i % n; return r < 0 ? r + n : r; }
 
-/* index of the point shifted by `off` along axis a, periodic wrap */
+/* Cell-centred Neumann: the node beyond a face is the mirror image of the node inside it
+ * (index -1 -> 0, -2 -> 1, n -> n-1, n+1 -> n-2), so every one-sided difference across
+ * the boundary vanishes, the discrete form of dc/dn = dmu/dn = 0 in Eq. (CH).            */
+static long mirror(long i, long n) {
+    if (i < 0) return -i - 1;
+    if (i >= n) return 2 * n - i - 1;
+    return i;
+}
+
+/* index of the point shifted by `off` along axis a (|off| <= n_a) */
 static long shift(const or_grid *g, long idx, int a, long off) {
-    long i0 = idx % g->n[0];
-    long i1 = (idx / g->n[0]) % g->n[1];
-    long i2 = idx / (g->n[0] * g->n[1]);
-    if (a == 0) i0 = wrap(i0 + off, g->n[0]);
-    if (a == 1) i1 = wrap(i1 + off, g->n[1]);
-    if (a == 2) i2 = wrap(i2 + off, g->n[2]);
-    return i0 + g->n[0] * (i1 + g->n[1] * i2);
+    long i[3];
+    i[0] = idx % g->n[0];
+    i[1] = (idx / g->n[0]) % g->n[1];
+    i[2] = idx / (g->n[0] * g->n[1]);
+    i[a] = g->bc ? mirror(i[a] + off, g->n[a]) : wrap(i[a] + off, g->n[a]);
+    return i[0] + g->n[0] * (i[1] + g->n[1] * i[2]);
 }
 
 /* Sec. 2, Eq. (IVP): A is symmetric positive semidefinite and -A is the discrete
- * Laplacian.  Standard second-order differences (Sec. 5.1), periodic wrap:
+ * Laplacian.  Standard second-order differences (Sec. 5.1), neighbours by shift():
  * (A v)_i = sum_a (2 v_i - v_{i+e_a} - v_{i-e_a}) / h_a^2.                            */
 void or_apply_A(const or_grid *g, const double *v, double *out) {
     long N = or_N(g);
@@ -710,8 +723,8 @@ int or_integrate(const or_grid *g, const or_params *prm, double *y, or_stats *st
 
 /* ------------------------------------------------------------------------------------ */
 /* Diagnostics (Sec. 5.2): discrete energy, Eq. (Ediscr) read as the Riemann sum of the  */
-/* energy functional of Eq. (Ee) with periodic forward differences, and the mass of      */
-/* Eq. (m) as h^d sum_i y_i.                                                             */
+/* energy functional of Eq. (Ee) with forward differences (periodic: n per axis; Neumann: */
+/* the n-1 interior ones, as Eq. (Ediscr) sums them), and the mass of Eq. (m), h^d sum y. */
 /* ------------------------------------------------------------------------------------ */
 double or_energy(const or_grid *g, const double *y) {
     long N = or_N(g);

@@ -5,7 +5,8 @@ baseline / reference arm of ``bench.py`` are the only callers.  Nothing in the C
 library imports this module, and this module imports nothing from the library.
 
 Parity status of each oracle routine (what pins it, see tests/test_oracle_*.py):
-  apply_A, rhs, ghat, jacvec   -- Fourier symbols (FFT), dense matrices, finite differences
+  apply_A, rhs, ghat, jacvec   -- Fourier symbols (FFT), dense matrices, finite differences;
+                                  Neumann grids: cosine-transform symbols, dense matrices
   lambda_max, cheb_order       -- dense ||A_hat||_1 and the LIM matvec counts printed in
                                   Tables 1 and 2 of the paper
   lim_step                     -- p = 1 reduces to explicit Euler; exact implicit-Euler modes
@@ -46,7 +47,8 @@ def build(force: bool = False) -> str:
 
 
 class OrGrid(C.Structure):
-    _fields_ = [("dim", C.c_int), ("n", C.c_long * 3), ("eps", C.c_double), ("eyre", C.c_int)]
+    _fields_ = [("dim", C.c_int), ("n", C.c_long * 3), ("eps", C.c_double), ("eyre", C.c_int),
+                ("bc", C.c_int)]
 
 
 class OrStats(C.Structure):
@@ -117,15 +119,19 @@ def lib():
     return _lib
 
 
-class Grid:
-    """Periodic grid on the unit square (dim=2) or cube (dim=3), h_a = 1/n_a."""
+BCS = ("periodic", "neumann")
 
-    def __init__(self, dim: int, n, eps: float, eyre: bool = False):
+
+class Grid:
+    """Grid on the unit square (dim=2) or cube (dim=3), h_a = 1/n_a, with periodic
+    boundaries or the homogeneous Neumann conditions of Eq. (CH) on cell-centred nodes."""
+
+    def __init__(self, dim: int, n, eps: float, eyre: bool = False, bc: str = "periodic"):
         n = [int(n)] * dim if np.isscalar(n) else [int(v) for v in n]
-        assert dim in (2, 3) and len(n) == dim
-        self.dim, self.n, self.eps, self.eyre = dim, tuple(n), float(eps), bool(eyre)
+        assert dim in (2, 3) and len(n) == dim and bc in BCS
+        self.dim, self.n, self.eps, self.eyre, self.bc = dim, tuple(n), float(eps), bool(eyre), bc
         nn = (n + [1, 1])[:3]
-        self._g = OrGrid(dim, (C.c_long * 3)(*nn), float(eps), int(eyre))
+        self._g = OrGrid(dim, (C.c_long * 3)(*nn), float(eps), int(eyre), BCS.index(bc))
         self.N = int(np.prod(n))
 
     @property

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ch_oracle.c")
 PINS = [os.path.join(ROOT, "tests", f) for f in
         ("test_oracle_operators.py", "test_oracle_krylov.py", "test_oracle_lim.py",
-         "test_oracle_drivers.py")]
+         "test_oracle_drivers.py", "test_oracle_neumann.py")]
 
 # (name, original text, planted text): the original must occur exactly once in ch_oracle.c
 MUTANTS = [
@@ -50,6 +50,12 @@ MUTANTS = [
      "? sqrt(prm->tol / est) * taken : taken;"),
     ("energy: gradient term doubled", "0.5 * g->eps * g->eps * sG", "g->eps * g->eps * sG"),
     ("mass: cell volume dropped", "return vol * s;", "return s;"),
+    ("Neumann: vertex-centred mirror at the low face", "if (i < 0) return -i - 1;",
+     "if (i < 0) return -i;"),
+    ("Neumann: vertex-centred mirror at the high face", "if (i >= n) return 2 * n - i - 1;",
+     "if (i >= n) return 2 * n - i - 2;"),
+    ("Neumann: periodic wrap kept", "i[a] = g->bc ? mirror(i[a] + off, g->n[a]) : wrap(i[a] + off, g->n[a]);",
+     "i[a] = wrap(i[a] + off, g->n[a]);"),
 ]
 
 
