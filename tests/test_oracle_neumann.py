@@ -186,19 +186,3 @@ def test_lim_counts_on_the_papers_neumann_grid(oracle, row):
     else:
         assert min(counts) <= printed <= max(counts)
 
-
-def test_constant_step_ee2_matvecs_of_table_1(oracle):
-    """Table 1, EE2 column, 64x64, tau = 0.25: printed 39138 matvecs with tol = 1e-6 (tol_phi by
-    Eq. tol_phi) and m_max = 100 over T = 1000 on the paper's Neumann grid.  The initial
-    state is random with an unpublished seed: over seeds 0..3 the Arnoldi products of this
-    run (one start-vector product per step excluded, which the paper obtains from f(y^n))
-    span 38403..39539, so the printed count is held to 3 %."""
-    n = 64
-    eps4 = 4 / (2 * np.sqrt(2) * np.arctanh(0.9))
-    g = oracle.Grid(2, (n, n), eps4 / 64, bc="neumann")
-    y0 = inputs.initial_state((n, n), 0, -0.01, 0.01)
-    rc, y, t, st, rec = oracle.integrate(g, y0, "ee2", False, 1000 / 64 ** 2, 0.25 / 64 ** 2,
-                                         tol=1e-6, mmax=100)
-    assert rc == 0 and st["steps"] == 4000 and st["restarts"] == 0
-    arnoldi = st["matvecs"] - st["steps"]
-    assert abs(arnoldi - 39138) < 0.03 * 39138, arnoldi
