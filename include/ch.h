@@ -99,6 +99,24 @@ ch_status ch_jacvec(ch_grid *g, const double *y_lin, const double *v, double *w,
 /* Fig. 1 step 1: lambda_max = ||A_hat(y)||_1 (host output, synchronises).                */
 ch_status ch_lambda_max(ch_grid *g, const double *y, int eyre, double *lambda_max);
 
+/* Host-only (no GPU needed).  Fig. 1 step 1 in the closed form the GPU path evaluates:
+ * every column of A_hat has an absolute sum g(d_j), d_j = 3 y_j^2 - 1 (+1 with Eyre), and g
+ * is convex, so ||A_hat||_1 = max(g(d_min), g(d_max)) from the extreme values y2min, y2max
+ * of y^2.  Periodic grid of dim 2/3 with n[a] in [4, 2^20] points per axis (n[2] ignored
+ * for dim 2), eps > 0.  CH_EINVAL for invalid arguments or y2min > y2max.               */
+ch_status ch_lambda_max_bound(int dim, const int64_t n[3], double eps, int eyre, double y2min,
+                              double y2max, double *lambda_max);
+
+/* Host-only (no GPU needed).  The schedule of one LIM step as the GPU path runs it
+ * (Fig. 1 steps 1, 2, 5): *p = the Chebyshev order of Eq. (p) for tau * lambda_max;
+ * order[k] (k < p, 1-based m) = the parameter used by the k-th iteration of steps 4-8
+ * (steps 9-12 reuse order[1..p-1]); a[m-1] = a_m.  order and a are caller-owned host
+ * arrays of `capacity` entries (either may be NULL).  capacity = 0 only reports p;
+ * 0 < capacity < p is CH_EINVAL.  CH_EINVAL also for tau not finite and > 0, a negative
+ * lambda_max or p above 10^6; CH_ENONFINITE for a non-finite lambda_max.                */
+ch_status ch_lim_schedule(double tau, double lambda_max, int capacity, int *p, int *order,
+                          double *a);
+
 /* Eq. (LIMest): est = ||y1 - y_PC|| / ||y_PC|| with
  * y_PC = y0 - (tau/2) A (F'(y0) + F'(y1) + eps^2 A (y0 + y1)).  Synchronises.             */
 ch_status ch_estimate(ch_grid *g, const double *y0, const double *y1, double tau, double *est);

@@ -53,6 +53,8 @@ _SIGS = {
     "ch_rhs": [_P, _P, _P, C.c_int, _DP, _DP],
     "ch_jacvec": [_P, _P, _P, _P, C.c_int],
     "ch_lambda_max": [_P, _P, C.c_int, _DP],
+    "ch_lambda_max_bound": [C.c_int, C.POINTER(C.c_int64), _D, C.c_int, _D, _D, _DP],
+    "ch_lim_schedule": [_D, _D, C.c_int, _IP, _IP, _DP],
     "ch_estimate": [_P, _P, _P, _D, _DP],
     "ch_phi_krylov": [_P, _P, _D, _D, C.c_int, C.c_int, C.c_int, _P, _DP, C.POINTER(ch_stats)],
     "ch_ee_step": [_P, _P, _D, C.POINTER(ch_params), _P, _DP, _DP],
@@ -178,6 +180,26 @@ def ch_lambda_max(h, y, eyre=0):
     out = C.c_double()
     _check(load().ch_lambda_max(h, _vec(h, y), int(eyre), C.byref(out)))
     return out.value
+
+
+def ch_lambda_max_bound(dim, n, eps, y2min, y2max, eyre=0):
+    """Host-only closed form of Fig. 1 step 1 from the extremes of y^2 (no GPU needed)."""
+    nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    out = C.c_double()
+    _check(load().ch_lambda_max_bound(dim, nn, eps, int(eyre), y2min, y2max, C.byref(out)))
+    return out.value
+
+
+def ch_lim_schedule(tau, lambda_max):
+    """Host-only LIM schedule of Fig. 1 (no GPU needed): (p, order (1-based m), a_m)."""
+    import numpy as np
+    p = C.c_int()
+    _check(load().ch_lim_schedule(tau, lambda_max, 0, C.byref(p), None, None))
+    order = np.zeros(p.value, np.int32)
+    a = np.zeros(p.value)
+    _check(load().ch_lim_schedule(tau, lambda_max, p.value, C.byref(p), order.ctypes.data_as(_IP),
+                                  a.ctypes.data_as(_DP)))
+    return p.value, order, a
 
 
 def ch_estimate(h, y0, y1, tau):

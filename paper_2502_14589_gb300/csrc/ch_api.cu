@@ -131,6 +131,27 @@ static ch_status check_launch() {
     return CH_OK;
 }
 
+// Grid geometry of the periodic unit square / cube, h_a = 1/n_a (arguments checked by the
+// caller): s_a = 1/h_a^2, kap_a = eps^2 s_a, sigma = 2 sum_a s_a.
+static void fill_geom(Geom &G, int dim, const int64_t n[3], double eps) {
+    memset(&G, 0, sizeof G);
+    G.dim = dim;
+    int64_t N = 1;
+    for (int a = 0; a < 3; ++a) {
+        G.n[a] = a < dim ? (int)n[a] : 1;
+        N *= G.n[a];
+    }
+    G.N = N;
+    G.st[0] = 1; G.st[1] = G.n[0]; G.st[2] = (int64_t)G.n[0] * G.n[1];
+    G.eps2 = eps * eps;
+    G.sigma = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        G.s[a] = (double)n[a] * (double)n[a];
+        G.kap[a] = G.eps2 * G.s[a];
+        G.sigma += 2.0 * G.s[a];
+    }
+}
+
 // Fig. 1 step 1 in closed form: column j of A_hat has the entries
 //   centre  d sigma + eps^2 (sigma^2 + 2 sum_a s_a^2),   +-e_a  -s_a (d + 2 eps^2 sigma),
 //   +-2e_a  eps^2 s_a^2,   +-e_a +-e_b  2 eps^2 s_a s_b   (distinct when every n_a >= 4),
@@ -415,18 +436,29 @@ static const std::vector<int> &cheb_param_order(int p) {
 // ---------------------------------------------------------------------------------------
 // LIM step (Sec. 3.1, Fig. 1) with lambda_max given.
 // ---------------------------------------------------------------------------------------
-static ch_status lim_step_impl(ch_grid *g, const double *yn, double tau, double lmax, int eyre,
-                               double *ynext, int *p_out) {
-    const Launch &L = g->L;
+// Fig. 1 steps 1, 2, 3 and 5 on the host: p by Eq. (p) and a_m = lmax (z_1 - beta_m)/(1 + z_1)
+// for m = 1..p with beta_m = cos(pi (2m - 1) / (2p)) and z_1 = beta_1.
+static ch_status lim_schedule(double tau, double lmax, int *p_out, std::vector<double> &a) {
     const double pi = 3.14159265358979323846;
     const int p = cheb_order(tau, lmax);                                   // step 1
     if (p < 1)
         return fail(isfinite(lmax) ? CH_EINVAL : CH_ENONFINITE,
                     "Chebyshev order for tau * lambda_max = %g out of range", tau * lmax);
-    std::vector<double> beta(p), a(p);
+    std::vector<double> beta(p);
+    a.assign(p, 0.0);
     for (int i = 1; i <= p; ++i) beta[i - 1] = cos(pi * (2.0 * i - 1.0) / (2.0 * p));   // 2
     const double z1 = beta[0];                                             // step 3
     for (int m = 1; m <= p; ++m) a[m - 1] = lmax / (1.0 + z1) * (z1 - beta[m - 1]);     // 5
+    *p_out = p;
+    return CH_OK;
+}
+
+static ch_status lim_step_impl(ch_grid *g, const double *yn, double tau, double lmax, int eyre,
+                               double *ynext, int *p_out) {
+    const Launch &L = g->L;
+    int p = 0;
+    std::vector<double> a;
+    CH_TRY(lim_schedule(tau, lmax, &p, a));
     ch::launch_prep(L, g->g, yn, eyre, g->D, g->G, 0);
     const std::vector<int> &order = cheb_param_order(p);                   // step 2
     const double *prev = yn;
@@ -600,6 +632,38 @@ const char *ch_last_error(void) { return g_last_error; }
 
 int64_t ch_kernel_launches(const ch_grid *g) { return g ? g->launches : 0; }
 
+ch_status ch_lim_schedule(double tau, double lambda_max, int capacity, int *p, int *order,
+                          double *a) {
+    if (!p) return fail(CH_EINVAL, "null argument");
+    if (!(tau > 0.0) || !isfinite(tau) || !(lambda_max >= 0.0))
+        return fail(CH_EINVAL, "tau must be finite and > 0, lambda_max >= 0");
+    int pp = 0;
+    std::vector<double> av;
+    CH_TRY(lim_schedule(tau, lambda_max, &pp, av));
+    *p = pp;
+    if (capacity < pp) return capacity == 0 ? CH_OK : fail(CH_EINVAL, "capacity %d < p = %d", capacity, pp);
+    const std::vector<int> &o = cheb_param_order(pp);
+    for (int k = 0; k < pp; ++k) {
+        if (order) order[k] = o[k];
+        if (a) a[k] = av[k];
+    }
+    return CH_OK;
+}
+
+ch_status ch_lambda_max_bound(int dim, const int64_t n[3], double eps, int eyre, double y2min,
+                              double y2max, double *lambda_max) {
+    if (!n || !lambda_max) return fail(CH_EINVAL, "null argument");
+    if (dim != 2 && dim != 3) return fail(CH_EINVAL, "dim must be 2 or 3");
+    for (int a = 0; a < dim; ++a)
+        if (n[a] < 4 || n[a] > (1 << 20)) return fail(CH_EINVAL, "n[%d] out of range [4, 2^20]", a);
+    if (!(eps > 0.0) || !isfinite(eps)) return fail(CH_EINVAL, "eps must be finite and > 0");
+    if (!(y2min >= 0.0) || !(y2max >= y2min)) return fail(CH_EINVAL, "need 0 <= y2min <= y2max");
+    Geom G;
+    fill_geom(G, dim, n, eps);
+    *lambda_max = lambda_from_minmax(G, y2min, y2max, eyre);
+    return CH_OK;
+}
+
 ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
                          int mmax_capacity, void *cuda_stream, ch_grid **out) {
     g_last_error[0] = 0;
@@ -617,18 +681,7 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
     if (mmax_capacity < 1 || mmax_capacity > 128) return fail(CH_EINVAL, "mmax_capacity must be in [1, 128]");
 
     ch_grid *g = new ch_grid();
-    memset(&g->g, 0, sizeof g->g);
-    g->g.dim = dim;
-    for (int a = 0; a < 3; ++a) g->g.n[a] = a < dim ? (int)n[a] : 1;
-    g->g.N = N;
-    g->g.st[0] = 1; g->g.st[1] = g->g.n[0]; g->g.st[2] = (int64_t)g->g.n[0] * g->g.n[1];
-    g->g.eps2 = eps * eps;
-    g->g.sigma = 0.0;
-    for (int a = 0; a < dim; ++a) {
-        g->g.s[a] = (double)n[a] * (double)n[a];
-        g->g.kap[a] = g->g.eps2 * g->g.s[a];
-        g->g.sigma += 2.0 * g->g.s[a];
-    }
+    fill_geom(g->g, dim, n, eps);
     g->precision = precision;
     g->mmax_cap = mmax_capacity;
     g->stream = (cudaStream_t)cuda_stream;
