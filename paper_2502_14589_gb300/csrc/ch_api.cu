@@ -309,6 +309,7 @@ static ch_status krylov_run_t(ch_grid *g, const double *y0, VT *slot0, VT *V, co
 static ch_status krylov_run(ch_grid *g, const double *y0, int s, double tau0,
                             double tol_phi_fixed, double tol, int use_ghat, int mmax,
                             double *ynext) {
+    ch::NvtxRange range("Krylov run (Fig. 2)");
     if (g->precision == CH_FP64) {
         CH_TRY(krylov_run_t<double>(g, y0, g->F[s], g->V, g->D, g->t, tau0, tol_phi_fixed, tol,
                                     use_ghat, mmax, ynext));
@@ -456,6 +457,7 @@ static ch_status lim_schedule(double tau, double lmax, int *p_out, std::vector<d
 static ch_status lim_step_impl(ch_grid *g, const double *yn, double tau, double lmax, int eyre,
                                double *ynext, int *p_out) {
     const Launch &L = g->L;
+    ch::NvtxRange range("LIM iterations (Fig. 1)");
     int p = 0;
     std::vector<double> a;
     CH_TRY(lim_schedule(tau, lmax, &p, a));
@@ -961,6 +963,7 @@ static double const_tau(double T, double tau0, int64_t k) {
 ch_status ch_integrate(ch_grid *g, const ch_params *prm, double *y, ch_stats *stats) {
     if (!g || !y) return fail(CH_EINVAL, "null argument");
     CH_TRY(check_params(g, prm));
+    ch::NvtxRange range(prm->scheme == CH_EE2 ? "ch_integrate EE2" : "ch_integrate LIM");
     ch_stats st;
     memset(&st, 0, sizeof st);
     g->rec.clear();

@@ -873,6 +873,7 @@ ch_status ch_integrate_batch(ch_batch *b, const ch_params *prm, double *y, ch_st
         return bfail(CH_EINVAL, "T and tau0 must be finite and > 0, tol > 0");
     if (prm->mmax < 1 || prm->mmax > b->mmax_cap) return bfail(CH_EINVAL, "mmax outside [1, capacity]");
     if (prm->max_steps < 1) return bfail(CH_EINVAL, "max_steps must be >= 1");
+    ch::NvtxRange range("ch_integrate_batch EE2");
     return b->precision == CH_MIXED ? integrate_b<float>(b, prm, y, stats)
                                     : integrate_b<double>(b, prm, y, stats);
 }

@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <vector>
@@ -21,6 +22,16 @@ namespace ch {
 constexpr int kThreads = 256;          // threads per block of the streaming kernels
 constexpr int kBlocksPerSM = 4;        // grid of the streaming kernels: 4 x 256 threads per SM
 constexpr int kMaxRed = 4;             // values reduced by one kernel at most
+
+// NVTX range over a host scope: the phases of the method (integration, Krylov run, LIM
+// iterations) appear as named ranges in profilers; without a profiler attached the
+// push/pop calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Periodic grid geometry, passed by value.  -A = discrete Laplacian, h_a = 1/n_a:
 //   (A v)_i = sum_a s_a (2 v_i - v_{i+e_a} - v_{i-e_a}),   s_a = 1/h_a^2 = n_a^2.
