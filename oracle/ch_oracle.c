@@ -17,7 +17,7 @@
  * nodes (Sec. 5.1: x_i = (i - 1/2) h), where a neighbour beyond the boundary is the mirror
  * image of the point inside it.
  *
- * Readings of points where the paper is silent (listed in the design doc as well):
+ * Readings of points where the paper is silent:
  *  - periodic boundary conditions for the benchmark workloads; the paper's Neumann
  *    conditions are the other choice of or_grid.bc;
  *  - "trace resnorm for s in [0,tau0]" (Fig. 2, RT algorithm) = halve s from the upper
