@@ -96,10 +96,11 @@ ch_status ch_rhs(ch_grid *g, const double *y, double *f, int eyre, double *norm_
 /* Eq. (A_g) / (A_g_cs): w = A_hat(y_lin) v = A (J + eps^2 A [+ I]) v.  Asynchronous.      */
 ch_status ch_jacvec(ch_grid *g, const double *y_lin, const double *v, double *w, int eyre);
 
-/* Fig. 1 step 1: lambda_max = ||A_hat(y)||_1 (host output, synchronises).                */
+/* Fig. 1, spectral bound: lambda_max = ||A_hat(y)||_1 (host output, synchronises).       */
 ch_status ch_lambda_max(ch_grid *g, const double *y, int eyre, double *lambda_max);
 
-/* Host-only (no GPU needed).  Fig. 1 step 1 in the closed form the GPU path evaluates:
+/* Host-only (no GPU needed).  The spectral bound of Fig. 1 in the closed form the GPU path
+ * evaluates:
  * every column of A_hat has an absolute sum g(d_j), d_j = 3 y_j^2 - 1 (+1 with Eyre), and g
  * is convex, so ||A_hat||_1 = max(g(d_min), g(d_max)) from the extreme values y2min, y2max
  * of y^2.  Periodic grid of dim 2/3 with n[a] in [4, 2^20] points per axis (n[2] ignored
@@ -108,9 +109,9 @@ ch_status ch_lambda_max_bound(int dim, const int64_t n[3], double eps, int eyre,
                               double y2max, double *lambda_max);
 
 /* Host-only (no GPU needed).  The schedule of one LIM step as the GPU path runs it
- * (Fig. 1 steps 1, 2, 5): *p = the Chebyshev order of Eq. (p) for tau * lambda_max;
- * order[k] (k < p, 1-based m) = the parameter used by the k-th iteration of steps 4-8
- * (steps 9-12 reuse order[1..p-1]); a[m-1] = a_m.  order and a are caller-owned host
+ * (Fig. 1): *p = the Chebyshev order of Eq. (p) for tau * lambda_max; order[k] (k < p,
+ * 1-based m) = the parameter used by the k-th iteration of the first sweep m = 1..p (the
+ * second sweep m = 2..p reuses order[1..p-1]); a[m-1] = a_m.  order and a are caller-owned host
  * arrays of `capacity` entries (either may be NULL).  capacity = 0 only reports p;
  * 0 < capacity < p is CH_EINVAL.  CH_EINVAL also for tau not finite and > 0, a negative
  * lambda_max or p above 10^6; CH_ENONFINITE for a non-finite lambda_max.                */
@@ -191,20 +192,20 @@ int64_t ch_batch_kernel_launches(const ch_batch *b);
 /* Kernel classes of the hot path, for launch accounting and timing (no counterpart in the
  * paper: these report where the time of Figs. 1-4 goes on the GPU). */
 typedef enum {
-    CH_K_PREP = 0,      /* D, G and min/max of y^2 from y^n (linearisation, Fig. 1 step 1) */
-    CH_K_TSTAGE,        /* stage 1 of A_hat v (Fig. 2 line 4) */
+    CH_K_PREP = 0,      /* D, G and min/max of y^2 from y^n (linearisation, bound of Fig. 1) */
+    CH_K_TSTAGE,        /* stage 1 of the Arnoldi product A_hat v (Fig. 2) */
     CH_K_WSTAGE,        /* stage 2 of A_hat v, fused with h_{1j} */
-    CH_K_MGS,           /* one modified Gram-Schmidt pass (Fig. 2 lines 5-9) */
-    CH_K_PHI,           /* projected phi, residual test, step trace (Fig. 2 lines 10-20) */
-    CH_K_COMBINE,       /* y^n + V_j (beta u) (Fig. 2 line 23) */
+    CH_K_MGS,           /* one modified Gram-Schmidt pass (Fig. 2) */
+    CH_K_PHI,           /* projected phi, residual test, step trace (Fig. 2) */
+    CH_K_COMBINE,       /* y^n + V_j (beta u), the Krylov combine (Fig. 2) */
     CH_K_RHS1,          /* stage 1 of f(y) (Eq. IVP) */
     CH_K_RHS2,          /* stage 2 of f(y), fused with norms and Eq. (LIMest) sums */
-    CH_K_RESID1,        /* stage 1 of g_hat - A_hat x (Fig. 1 steps 6/10, restarts) */
+    CH_K_RESID1,        /* stage 1 of g_hat - A_hat x (LIM update of Fig. 1, restarts) */
     CH_K_RESID2,        /* stage 2 of g_hat - A_hat x with its norm (restart vector) */
-    CH_K_LIM2,          /* stage 2 fused with the LIM update (Fig. 1 steps 6/10) */
+    CH_K_LIM2,          /* stage 2 fused with the LIM update (Fig. 1) */
     CH_K_ENERGY,        /* energy and mass */
     CH_K_ARM,           /* Krylov start: beta, tol_phi (Eq. tol_phi) */
-    CH_K_ARNOLDI,       /* a whole Arnoldi iteration (Fig. 2 lines 4-9) in one launch
+    CH_K_ARNOLDI,       /* a whole Arnoldi iteration (Fig. 2) in one launch
                            (sequential passes; Gram-corrected on FP32 grids, j <= 31) */
     CH_K_COUNT
 } ch_kernel_class;

@@ -25,7 +25,7 @@
  *    the admissible end;
  *  - constant-step EE2 uses linear residual-time restarting over the whole step with
  *    A_hat, g_hat frozen at y^n;
- *  - the order of beta_2..beta_p (Fig. 1 step 2) bounds round-off growth (or_lim_order);
+ *  - the order of beta_2..beta_p (left open by Fig. 1) bounds round-off growth (or_lim_order);
  *  - beta == 0 gives y^{n+1} = y^n; est == 0 keeps tau (LIM) or takes 5/4 tau (EE2);
  *  - a step clipped to end at T sets t := T exactly.
  */
@@ -146,7 +146,7 @@ void or_jacvec(const or_grid *g, const double *yn, const double *v, double *w) {
 /* LIM (Sec. 3, Fig. 1)                                                                 */
 /* ------------------------------------------------------------------------------------ */
 
-/* Fig. 1 step 1: lambda_max := ||A_hat_n||_1 = max_j sum_i |a_ij|, computed by forming
+/* Fig. 1, spectral bound: lambda_max := ||A_hat_n||_1 = max_j sum_i |a_ij|, computed by forming
  * every column A_hat_n e_j explicitly.  A column has at most 13 (2D) or 25 (3D) nonzeros;
  * they are gathered into a small list, summing entries whose periodic indices coincide
  * (which happens on grids with fewer than 5 points along an axis).                      */
@@ -225,7 +225,7 @@ static void dense_matvec(void *ctx, const double *v, double *w) {
     }
 }
 
-/* Fig. 1 step 2 asks for an ORDERED set {beta_m} and fixes only beta_1 = cos(pi/2p) (so
+/* Fig. 1 asks for an ORDERED set {beta_m} and fixes only beta_1 = cos(pi/2p) (so
  * that a_1 = 0 comes first).  Every LIM iteration maps the error against the implicit-
  * Euler solution of Eq. (EBlin) by the factor (tau a_m - tau A_hat)/(1 + tau a_m); these
  * factors commute, so the order of beta_2..beta_p does not change the step in exact
@@ -239,7 +239,7 @@ static void dense_matvec(void *ctx, const double *v, double *w) {
  *   order(p), m = floor(p/2): for each j of order(m) in turn, the pair (j, p + 1 - j);
  *   for odd p the middle index m + 1 is inserted right after the first pair.
  * It starts with m = 1, as Fig. 1 requires, and keeps the growth of iterates times the
- * amplification of later factors near (tau*lambda_max)^2.  The second sweep (steps 9-12)
+ * amplification of later factors near (tau*lambda_max)^2.  The second sweep (m = 2..p)
  * reuses the order without m = 1.  order[] receives 0-based m.                          */
 #define OR_LIM_MAX_P 1000000
 static void lim_order_rec(int p, int *out) {               /* 1-based, length p */
@@ -262,29 +262,29 @@ int or_lim_order(int p, int *order) {
     return 0;
 }
 
-/* Fig. 1 steps 2-13: one LIM step for y' = -A_hat y + g_hat, y(0) = y^n, with a given
+/* Fig. 1: one LIM step for y' = -A_hat y + g_hat, y(0) = y^n, with a given
  * spectral bound lambda_max.  Returns p (or -1 when p exceeds OR_LIM_MAX_P).           */
 static int lim_core(or_matvec_fn mv, void *ctx, long N, const double *ghat,
                     const double *yn, double tau, double lambda_max, double *ynext,
                     long *matvecs) {
     const double pi = 3.14159265358979323846;
-    int p = or_cheb_order(tau, lambda_max);                        /* step 1 */
+    int p = or_cheb_order(tau, lambda_max);                        /* Eq. (p) */
     int *order = malloc(p * sizeof(int));
-    if (or_lim_order(p, order) != 0) { free(order); return -1; }   /* step 2 */
+    if (or_lim_order(p, order) != 0) { free(order); return -1; }   /* ordered set */
     double *beta = malloc(p * sizeof(double)), *a = malloc(p * sizeof(double));
     for (int i = 1; i <= p; ++i) beta[i - 1] = cos(pi * (2.0 * i - 1.0) / (2.0 * p));
-    double z1 = beta[0];                                           /* step 3 */
-    for (int m = 1; m <= p; ++m) a[m - 1] = lambda_max / (1.0 + z1) * (z1 - beta[m - 1]); /* 5 */
+    double z1 = beta[0];                                           /* z_1 */
+    for (int m = 1; m <= p; ++m) a[m - 1] = lambda_max / (1.0 + z1) * (z1 - beta[m - 1]); /* a_m */
     double *prev = malloc(N * sizeof(double)), *Ay = malloc(N * sizeof(double));
-    memcpy(prev, yn, N * sizeof(double));                          /* step 3 */
-    for (int sweep = 0; sweep < 2; ++sweep) {                      /* steps 4-8, 9-12 */
+    memcpy(prev, yn, N * sizeof(double));                          /* y(prev) := y^n */
+    for (int sweep = 0; sweep < 2; ++sweep) {                      /* m = 1..p, then 2..p */
         for (int idx = (sweep == 0 ? 0 : 1); idx < p; ++idx) {
             double am = a[order[idx]];
             mv(ctx, prev, Ay); ++*matvecs;
-            for (long i = 0; i < N; ++i)                           /* steps 6 and 10 */
+            for (long i = 0; i < N; ++i)                           /* the LIM update */
                 ynext[i] = (yn[i] + tau * am * prev[i] + tau * (ghat[i] - Ay[i]))
                            / (1.0 + tau * am);
-            memcpy(prev, ynext, N * sizeof(double));               /* steps 7 and 11 */
+            memcpy(prev, ynext, N * sizeof(double));               /* y(prev) := y(next) */
         }
     }
     free(order); free(beta); free(a); free(prev); free(Ay);
@@ -427,7 +427,7 @@ static double dot(long N, const double *a, const double *b) {
     return acc;
 }
 
-/* Fixed search rule for Fig. 2 lines 16-17 ("trace resnorm for s in [0, tau0]"):
+/* Fixed search rule for the step trace of Fig. 2 ("trace resnorm for s in [0, tau0]"):
  * halve s from s_max until resnorm(s) <= tol, at most OR_MAX_HALVINGS times, then
  * OR_BISECTIONS bisection steps between that admissible s and the last rejected one,
  * keeping the admissible end.                                                           */
@@ -437,23 +437,23 @@ static double dot(long N, const double *a, const double *b) {
 static double resnorm_at(int j, const double *H, int ldh, double hnext, double s,
                          double *u, long *phi_evals) {
     or_phi_e1(j, H, ldh, s, u); ++*phi_evals;
-    return hnext * fabs(u[j - 1]);                     /* Fig. 2 line 12 */
+    return hnext * fabs(u[j - 1]);                     /* resnorm of Fig. 2 */
 }
 
 /* One run of the Arnoldi loop of Fig. 2 for y' = -A_hat y + g, y(0) = y0, with starting
- * vector v_1 = g - A_hat y0 (line 2).  The tentative step is tau0.  On return *tau is
+ * vector v_1 = g - A_hat y0.  The tentative step is tau0.  On return *tau is
  * the step taken (tau0, or the largest admissible s < tau0 found by the trace) and
- * ynext = y0 + V_j (beta u) (line 23).  *jexit is the Krylov dimension j at exit.
+ * ynext = y0 + V_j (beta u).  *jexit is the Krylov dimension j at exit.
  * Returns 0 ok, 4 when no admissible s is found.                                        */
 static int krylov_core(or_matvec_fn mv, void *ctx, long N, const double *g,
                        const double *y0, double tau0, double tol_phi, int mmax,
                        double *ynext, double *tau, int *jexit, or_stats *st) {
     int ldh = mmax;                                                /* H is (mmax+1) x mmax */
-    double *H = calloc((size_t)(mmax + 1) * mmax, sizeof(double)); /* line 1 */
+    double *H = calloc((size_t)(mmax + 1) * mmax, sizeof(double)); /* H := 0 */
     double *V = calloc((size_t)N * (mmax + 1), sizeof(double));    /* column k at V + k*N */
     double *w = malloc(N * sizeof(double)), *u = calloc(mmax, sizeof(double));
     int rc = 0;
-    mv(ctx, y0, w); ++st->matvecs;                                 /* line 2 */
+    mv(ctx, y0, w); ++st->matvecs;                                 /* start vector */
     for (long i = 0; i < N; ++i) V[i] = g[i] - w[i];
     double beta = sqrt(dot(N, V, V));
     *tau = tau0;
@@ -464,23 +464,23 @@ static int krylov_core(or_matvec_fn mv, void *ctx, long N, const double *g,
     }
     for (long i = 0; i < N; ++i) V[i] /= beta;
     int j;
-    for (j = 1; j <= mmax; ++j) {                                  /* line 3 */
+    for (j = 1; j <= mmax; ++j) {                                  /* Arnoldi loop */
         double *vj = V + (size_t)(j - 1) * N;
-        mv(ctx, vj, w); ++st->matvecs; ++st->krylov_iters;          /* line 4 */
-        for (int i = 1; i <= j; ++i) {                             /* lines 5-8 */
+        mv(ctx, vj, w); ++st->matvecs; ++st->krylov_iters;          /* w := A_hat v_j */
+        for (int i = 1; i <= j; ++i) {                             /* modified Gram-Schmidt */
             double *vi = V + (size_t)(i - 1) * N;
             double hij = dot(N, w, vi);
             H[(i - 1) * ldh + (j - 1)] = hij;
             for (long k = 0; k < N; ++k) w[k] -= hij * vi[k];
         }
-        double hnext = sqrt(dot(N, w, w));                         /* line 9 */
+        double hnext = sqrt(dot(N, w, w));                         /* h_{j+1,j} */
         H[j * ldh + (j - 1)] = hnext;
-        double s = tau0;                                           /* line 11 */
-        double resnorm = resnorm_at(j, H, ldh, hnext, s, u, &st->phi_evals); /* line 12 */
-        if (resnorm <= tol_phi) {                                  /* lines 13-14 */
+        double s = tau0;                                           /* s := tau0 */
+        double resnorm = resnorm_at(j, H, ldh, hnext, s, u, &st->phi_evals); /* resnorm */
+        if (resnorm <= tol_phi) {                                  /* converged */
             *tau = tau0;
             break;
-        } else if (j == mmax) {                                    /* lines 15-19 */
+        } else if (j == mmax) {                                    /* step trace */
             double lo = tau0, hi = tau0;
             int ok = 0;
             for (int k = 0; k < OR_MAX_HALVINGS; ++k) {
@@ -493,16 +493,16 @@ static int krylov_core(or_matvec_fn mv, void *ctx, long N, const double *g,
                 if (resnorm_at(j, H, ldh, hnext, mid, u, &st->phi_evals) <= tol_phi) lo = mid;
                 else hi = mid;
             }
-            *tau = lo;                                             /* line 17 */
-            resnorm_at(j, H, ldh, hnext, lo, u, &st->phi_evals);   /* line 18 */
+            *tau = lo;                                             /* tau := s */
+            resnorm_at(j, H, ldh, hnext, lo, u, &st->phi_evals);   /* u at s */
             break;
         }
-        double *vnext = V + (size_t)j * N;                         /* line 21 */
+        double *vnext = V + (size_t)j * N;                         /* v_{j+1} := w / h_{j+1,j} */
         for (long k = 0; k < N; ++k) vnext[k] = w[k] / hnext;
     }
     if (j > mmax) j = mmax;
     *jexit = j;
-    if (rc == 0) {                                                 /* line 23 */
+    if (rc == 0) {                                                 /* y0 + V_j (beta u) */
         for (long k = 0; k < N; ++k) {
             double acc = 0.0;
             for (int c = 0; c < j; ++c) acc += V[(size_t)c * N + k] * (beta * u[c]);
@@ -524,7 +524,7 @@ int or_krylov_dense(long N, const double *M, const double *g, const double *y0, 
     return krylov_core(dense_matvec, &op, N, g, y0, tau0, tol_phi, mmax, ynext, tau, jexit, &st);
 }
 
-/* Arnoldi relation check for tests: runs lines 2-9 and 21 of Fig. 2 for exactly m
+/* Arnoldi relation check for tests: runs the Arnoldi process of Fig. 2 for exactly m
  * iterations (no residual test) and returns V (N x (m+1), column-major by vector) and
  * H ((m+1) x m row-major).                                                            */
 int or_arnoldi_dense(long N, const double *M, const double *v1, int m, double *V, double *H) {
@@ -559,7 +559,7 @@ double or_tol_phi(double norm_ghat, double beta, double tol) {
 
 /* One EE2 step (Sec. 4.1, Eqs. IVPlin, EE2, Fig. 2) on the grid operator.
  * linear_restart = 0: nonlinear RT restarting -- the Krylov run may shrink tau and the
- *   shrunken step is taken (the adaptive scheme, Fig. 4 step 7).
+ *   shrunken step is taken (the adaptive scheme of Fig. 4 takes the step the Krylov run returns).
  * linear_restart = 1: linear RT restarting over the whole step tau (constant-step use,
  *   end of Sec. 4.1): A_hat_n, g_hat^n stay frozen at y^n; whenever a run cannot reach
  *   the remaining time it advances by its admissible s and restarts from there with
@@ -661,26 +661,26 @@ int or_integrate(const or_grid *g, const or_params *prm, double *y, or_stats *st
                  or_records *rec, double *t_out) {
     long N = or_N(g);
     double *ynext = malloc(N * sizeof(double));
-    double t = 0.0, tau = prm->tau0;                                 /* step 1 */
+    double t = 0.0, tau = prm->tau0;                                 /* t := 0, tau := tau0 */
     long nconst = prm->adaptive ? 0 : or_const_nsteps(prm->T, prm->tau0);
     int rc = 0;
     memset(st, 0, sizeof *st);
     for (;;) {
-        if (prm->adaptive ? !(t < prm->T) : st->steps >= nconst) break;   /* step 2 */
+        if (prm->adaptive ? !(t < prm->T) : st->steps >= nconst) break;   /* while t < T */
         int clipped = 0;
         if (prm->adaptive) {
-            if (t + tau > prm->T) { tau = prm->T - t; clipped = 1; }       /* steps 3-5 */
+            if (t + tau > prm->T) { tau = prm->T - t; clipped = 1; }       /* clip to T */
         } else {
             tau = or_const_tau(prm->T, prm->tau0, st->steps);
         }
         double taken = tau, est = 0.0, lmax = 0.0;
         int jexit = 0, p = 0;
         long restarts_before = st->restarts, shrinks_before = st->tau_shrinks;
-        if (prm->scheme == 0) {                                      /* steps 6-7, Fig. 4 */
+        if (prm->scheme == 0) {                                      /* EE2 step, Fig. 4 */
             int lin = prm->adaptive ? 0 : 1;
             rc = or_ee_step(g, y, tau, prm->tol, prm->tol_phi, prm->mmax, lin, ynext,
                             &taken, &jexit, st);
-        } else {                                                     /* steps 6-7, Fig. 3 */
+        } else {                                                     /* LIM step, Fig. 3 */
             p = or_lim_step(g, y, tau, ynext, &lmax, &st->matvecs);
             if (p < 0) rc = 4;
         }
@@ -688,7 +688,7 @@ int or_integrate(const or_grid *g, const or_params *prm, double *y, or_stats *st
         for (long i = 0; i < N; ++i)
             if (!isfinite(ynext[i])) { rc = 5; break; }
         if (rc != 0) break;
-        if (prm->adaptive) {                                         /* step 8 */
+        if (prm->adaptive) {                                         /* est, Eq. (LIMest) */
             est = or_estimate(g, y, ynext, taken);
             st->rhs_evals += 1;
             if (!isfinite(est)) { rc = 5; break; }
@@ -699,11 +699,11 @@ int or_integrate(const or_grid *g, const or_params *prm, double *y, or_stats *st
             rec->restarts[k] = (int)(st->restarts - restarts_before);
             rec->shrunk[k] = (int)(st->tau_shrinks - shrinks_before);
         }
-        memcpy(y, ynext, N * sizeof(double));                        /* step 9 */
+        memcpy(y, ynext, N * sizeof(double));                        /* accept */
         if (prm->adaptive) t = (clipped && taken == tau) ? prm->T : t + taken;
         else t = (st->steps + 1 == nconst) ? prm->T : t + taken;
         ++st->steps;
-        if (prm->adaptive) {                                         /* step 10 */
+        if (prm->adaptive) {                                         /* next tau */
             if (prm->scheme == 0) {                                  /* Eq. (EEdt) */
                 double grow = 1.25 * taken;
                 tau = (est > 0.0) ? fmin(grow, sqrt(prm->tol / est) * taken) : grow;

@@ -172,7 +172,7 @@ def lambda_max(g: Grid, y) -> float:
 
 
 def column_abs_sum(g: Grid, y, j: int) -> float:
-    """Absolute sum of column j of A_hat_n (Fig. 1 step 1 for one column)."""
+    """Absolute sum of column j of A_hat_n (the spectral bound of Fig. 1, one column)."""
     return lib().or_column_abs_sum(g.ptr(), g._vec(y), int(j))
 
 
@@ -181,7 +181,7 @@ def cheb_order(tau: float, lmax: float) -> int:
 
 
 def lim_order(p: int):
-    """0-based order of the Chebyshev parameters used by the LIM step (Fig. 1 step 2)."""
+    """0-based order of the Chebyshev parameters used by the LIM step (the ordered set of Fig. 1)."""
     o = np.zeros(p, dtype=np.int32)
     assert lib().or_lim_order(p, o) == 0
     return o

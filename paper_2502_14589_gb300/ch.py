@@ -183,7 +183,7 @@ def ch_lambda_max(h, y, eyre=0):
 
 
 def ch_lambda_max_bound(dim, n, eps, y2min, y2max, eyre=0):
-    """Host-only closed form of Fig. 1 step 1 from the extremes of y^2 (no GPU needed)."""
+    """Host-only closed form of the spectral bound of Fig. 1 from the extremes of y^2 (no GPU needed)."""
     nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
     out = C.c_double()
     _check(load().ch_lambda_max_bound(dim, nn, eps, int(eyre), y2min, y2max, C.byref(out)))

@@ -57,7 +57,7 @@ struct StepRecord {
     int jexit, restarts, shrunk, p;
 };
 
-// One captured Arnoldi iteration (Fig. 2 lines 4-20 for a fixed j) and what it launches.
+// One captured Arnoldi iteration (Fig. 2, a fixed j with its residual test) and what it launches.
 struct IterGraph {
     cudaGraphExec_t exec = nullptr;
     int64_t launches = 0;
@@ -152,7 +152,7 @@ static void fill_geom(Geom &G, int dim, const int64_t n[3], double eps) {
     }
 }
 
-// Fig. 1 step 1 in closed form: column j of A_hat has the entries
+// The spectral bound of Fig. 1 in closed form: column j of A_hat has the entries
 //   centre  d sigma + eps^2 (sigma^2 + 2 sum_a s_a^2),   +-e_a  -s_a (d + 2 eps^2 sigma),
 //   +-2e_a  eps^2 s_a^2,   +-e_a +-e_b  2 eps^2 s_a s_b   (distinct when every n_a >= 4),
 // so its absolute sum g(d) is convex in d and ||A_hat||_1 = max(g(d_min), g(d_max)).
@@ -194,14 +194,14 @@ static void rhs(ch_grid *g, const double *y, double *out, int eyre, int mode,
 // red[1] = ||g_hat||^2 when use_ghat).  Dm must hold the linearisation coefficients in the
 // basis precision VT.  The result y0 + V_j (beta u) is written to ynext (FP64); the run's
 // scalars are left in ctrl (not synchronised).
-// Krylov dimensions evaluated together by one projected-phi launch (Fig. 2 lines 10-14 for
+// Krylov dimensions evaluated together by one projected-phi launch (Fig. 2, projected phi and residual test for
 // j0..j0+7 from the same H, one cluster each).  Iterations past the j at exit are
 // speculative work: their A_hat products are not counted as matvecs and their basis
 // columns are never combined.  Eight per launch halves the phi launches of a run to m_max
 // = 30 against four, for at most four more speculative iterations when a run stops early.
 constexpr int kPhiBlock = 8;
 
-// Kernels of Arnoldi iterations j0..j1 (Fig. 2 lines 4-9, 21), the projected phi and residual
+// Kernels of Arnoldi iterations j0..j1 (Fig. 2), the projected phi and residual
 // tests of those dimensions, and the copy of the device `active` flag to pinned memory.
 template <typename VT>
 static void queue_block(ch_grid *g, const Launch &L, VT *slot0, VT *V, const VT *Dm, VT *t,
@@ -385,7 +385,7 @@ static ch_status ee_step_impl(ch_grid *g, const double *yn, int cur, double tau,
             ycur = dst;
             dst = (dst == ynext) ? g->y[0] : (dst == g->y[0] ? g->y[1] : g->y[0]);
             if (++restarts > 100000) return fail(CH_ENOTCONV, "linear restart cap reached");
-            // restart vector W_1 = g_hat^n - A_hat_n y_cur (Fig. 2 line 2)
+            // restart vector W_1 = g_hat^n - A_hat_n y_cur (the start vector of Fig. 2)
             slot = 1 - cur;
             ch::launch_resid1(L, g->g, ycur, g->D, g->G, g->t);
             ch::launch_resid2(L, g->g, g->t, g->F[slot]);
@@ -406,7 +406,7 @@ static ch_status ee_step_impl(ch_grid *g, const double *yn, int cur, double tau,
 }
 
 // ---------------------------------------------------------------------------------------
-// Order of the Chebyshev parameters (Fig. 1 step 2 fixes only beta_1 first).  The factors
+// Order of the Chebyshev parameters (Fig. 1 fixes only beta_1 first).  The factors
 // of the LIM iterations commute, so the order changes only the growth of rounding errors;
 // this is the recursive mirror-pair order of Lebedev and Finogenov (1971), extended to odd
 // p by placing the middle index right after the first pair.  1-based indices, cached per p.
@@ -437,18 +437,18 @@ static const std::vector<int> &cheb_param_order(int p) {
 // ---------------------------------------------------------------------------------------
 // LIM step (Sec. 3.1, Fig. 1) with lambda_max given.
 // ---------------------------------------------------------------------------------------
-// Fig. 1 steps 1, 2, 3 and 5 on the host: p by Eq. (p) and a_m = lmax (z_1 - beta_m)/(1 + z_1)
+// Fig. 1 on the host: p by Eq. (p) and a_m = lmax (z_1 - beta_m)/(1 + z_1)
 // for m = 1..p with beta_m = cos(pi (2m - 1) / (2p)) and z_1 = beta_1.
 static ch_status lim_schedule(double tau, double lmax, int *p_out, std::vector<double> &a) {
     const double pi = 3.14159265358979323846;
-    const int p = cheb_order(tau, lmax);                                   // step 1
+    const int p = cheb_order(tau, lmax);                                   // Eq. (p)
     if (p < 1)
         return fail(isfinite(lmax) ? CH_EINVAL : CH_ENONFINITE,
                     "Chebyshev order for tau * lambda_max = %g out of range", tau * lmax);
     std::vector<double> beta(p);
     a.assign(p, 0.0);
     for (int i = 1; i <= p; ++i) beta[i - 1] = cos(pi * (2.0 * i - 1.0) / (2.0 * p));   // 2
-    const double z1 = beta[0];                                             // step 3
+    const double z1 = beta[0];                                             // z_1
     for (int m = 1; m <= p; ++m) a[m - 1] = lmax / (1.0 + z1) * (z1 - beta[m - 1]);     // 5
     *p_out = p;
     return CH_OK;
@@ -462,11 +462,11 @@ static ch_status lim_step_impl(ch_grid *g, const double *yn, double tau, double 
     std::vector<double> a;
     CH_TRY(lim_schedule(tau, lmax, &p, a));
     ch::launch_prep(L, g->g, yn, eyre, g->D, g->G, 0);
-    const std::vector<int> &order = cheb_param_order(p);                   // step 2
+    const std::vector<int> &order = cheb_param_order(p);                   // ordered set
     const double *prev = yn;
     int it = 0;
     const int total = 2 * p - 1;
-    for (int sweep = 0; sweep < 2; ++sweep) {                              // steps 4-12
+    for (int sweep = 0; sweep < 2; ++sweep) {                              // m = 1..p, 2..p
         for (int idx = (sweep == 0 ? 0 : 1); idx < p; ++idx) {
             ++it;
             double *next = (it == total) ? ynext : g->y[it & 1];
@@ -967,7 +967,7 @@ ch_status ch_integrate(ch_grid *g, const ch_params *prm, double *y, ch_stats *st
     ch_stats st;
     memset(&st, 0, sizeof st);
     g->rec.clear();
-    double t = g->resume ? g->t_resume : 0.0;                              // step 1
+    double t = g->resume ? g->t_resume : 0.0;                              // t := 0
     double tau = g->resume ? g->tau_resume : prm->tau0;
     g->resume = 0;
     const int adaptive = prm->adaptive, eyre = prm->eyre;
@@ -990,16 +990,16 @@ ch_status ch_integrate(ch_grid *g, const ch_params *prm, double *y, ch_stats *st
     }
     ch_status rc = CH_OK;
     for (;;) {
-        if (adaptive ? !(t < prm->T) : st.steps >= nconst) break;         // step 2
+        if (adaptive ? !(t < prm->T) : st.steps >= nconst) break;         // while t < T
         int clipped = 0;
         if (adaptive) {
-            if (t + tau > prm->T) { tau = prm->T - t; clipped = 1; }      // steps 3-5
+            if (t + tau > prm->T) { tau = prm->T - t; clipped = 1; }      // clip to T
         } else {
             tau = const_tau(prm->T, prm->tau0, st.steps);
         }
         StepRecord r = {tau, 0.0, 0, 0, 0, 0};
         double taken = tau, est = 0.0;
-        if (prm->scheme == CH_EE2) {                                       // steps 6-8, Fig. 4
+        if (prm->scheme == CH_EE2) {                                       // EE2 step, Fig. 4
             EEOut o;
             rc = ee_step_impl(g, ycur, cur, tau, prm->tol_phi, prm->tol, prm->mmax, !adaptive,
                               eyre, ynew, adaptive, &o);
@@ -1016,7 +1016,7 @@ ch_status ch_integrate(ch_grid *g, const ch_params *prm, double *y, ch_stats *st
                 rhs(g, ynew, g->F[cur], eyre, 1 | (use_ghat ? 2 : 0));
                 st.rhs_evals += 1;
             }
-        } else {                                                           // steps 6-8, Fig. 3
+        } else {                                                           // LIM step, Fig. 3
             int p = 0;
             rc = lim_step_impl(g, ycur, tau, lmax, eyre, ynew, &p);
             if (rc != CH_OK) break;
@@ -1043,11 +1043,11 @@ ch_status ch_integrate(ch_grid *g, const ch_params *prm, double *y, ch_stats *st
         if (adaptive && !isfinite(est)) { rc = fail(CH_ENONFINITE, "non-finite error estimate"); break; }
         r.tau = taken; r.est = est;
         add_record(g, r);
-        std::swap(ycur, ynew);                                             // step 9
+        std::swap(ycur, ynew);                                             // accept
         if (adaptive) t = (clipped && taken == tau) ? prm->T : t + taken;
         else t = (st.steps + 1 == nconst) ? prm->T : t + taken;
         ++st.steps;
-        if (adaptive) {                                                    // step 10
+        if (adaptive) {                                                    // next tau
             if (prm->scheme == CH_EE2) {                                   // Eq. (EEdt)
                 const double grow = 1.25 * taken;
                 tau = (est > 0.0) ? std::min(grow, sqrt(prm->tol / est) * taken) : grow;

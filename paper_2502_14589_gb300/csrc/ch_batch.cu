@@ -47,7 +47,7 @@ struct Chunk {
     int pad;
 };
 
-// Per-instance step state (Fig. 4 steps 1-10) and counters.
+// Per-instance step state (Fig. 4) and counters.
 struct BState {
     double t, tau, est;
     int done, clipped, status, pad;
@@ -252,7 +252,7 @@ kb_rhs2(const Inst *insts, const Chunk *chunks, const BState *bs, Ctrl *ctrls,
     });
 }
 
-// ---- Krylov start of every instance still before T: Fig. 4 steps 3-5 and Fig. 2 line 2 --
+// ---- Krylov start of every instance still before T: clipping (Fig. 4), start vector (Fig. 2)
 __global__ void kb_arm(Ctrl *ctrls, BState *bs, int count, double T, double tol_phi_fixed,
                        double tol) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -281,7 +281,7 @@ __global__ void kb_arm(Ctrl *ctrls, BState *bs, int count, double T, double tol_
     c->gam[0] = beta > 0.0 ? 1.0 / beta : 0.0;
 }
 
-// ---- Arnoldi iteration (Fig. 2 lines 4-9), per chunk of the still-active instances --------
+// ---- Arnoldi iteration (Fig. 2), per chunk of the still-active instances ------------------
 template <int DIM, typename VT>
 __global__ void __launch_bounds__(kThreads)
 kb_tstage(const Inst *insts, const Chunk *chunks, const Ctrl *ctrls, const VT *__restrict__ x,
@@ -378,7 +378,7 @@ kb_mgs(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, VT *__restrict__ w,
         double v[1] = {acc.value()};
         inst_sum<1>(v, I, ck.inst, partials, nct, tickets, [&](double (&tot)[1]) {
             ctrl->hnext2 = tot[0];
-            H[j * ldh + (j - 1)] = sqrt(tot[0]);          // Fig. 2 line 9
+            H[j * ldh + (j - 1)] = sqrt(tot[0]);          // h_{j+1,j} (Fig. 2)
         });
     }
 }
@@ -394,7 +394,7 @@ __global__ void kb_any(const Ctrl *ctrls, int count, int *flag) {
     if (threadIdx.x == 0) *flag = any;
 }
 
-// ---- Fig. 2 line 23 per instance; finished instances carry y over -------------------------
+// ---- Krylov combine of Fig. 2 per instance; finished instances carry y over ---------------
 template <typename VT>
 __global__ void __launch_bounds__(kThreads)
 kb_combine(const Inst *insts, const Chunk *chunks, const BState *bs, Ctrl *ctrls,
@@ -444,7 +444,7 @@ kb_combine32b(const Inst *insts, const Chunk *chunks, const BState *bs, const Ct
     }
 }
 
-// ---- Fig. 4 steps 8-10 per instance: est, time, next step size (Eq. EEdt), counters -------
+// ---- Fig. 4 per instance: est, time, next step size (Eq. EEdt), counters -----------------
 __global__ void kb_control(Ctrl *ctrls, BState *bs, int count, double T, double tol,
                            int *remaining) {
     __shared__ int rem;

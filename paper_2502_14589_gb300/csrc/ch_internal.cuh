@@ -53,20 +53,20 @@ struct Ctrl {
     int active;         // 1 while the Arnoldi loop of Fig. 2 runs
     int jexit;          // Krylov dimension j at exit
     int status;         // ch_status of the last device-side failure (0 = none)
-    int converged;      // 1: resnorm(tau0) <= tol_phi (Fig. 2 lines 13-14)
-    int shrunk;         // 1: the trace of lines 15-19 cut the step
+    int converged;      // 1: resnorm(tau0) <= tol_phi (the residual test of Fig. 2)
+    int shrunk;         // 1: the step trace of Fig. 2 cut the step
     int phi_evals;      // projected-phi evaluations of this run
     int pad[2];
     double tau0;        // tentative step of this run
     double tol_phi;
     double tau;         // step taken by this run
-    double beta;        // ||v_1|| (Fig. 2 line 2)
+    double beta;        // ||v_1|| (the start vector of Fig. 2)
     double rinv;        // 1/beta, then 1/h_{j+1,j}: scale of the next basis vector
     double hnext2;      // ||w||^2 of the last Arnoldi iteration
     double resnorm;
     double red[8];      // generic reduced scalars (norms, est sums, min/max)
     double gam[130];    // v_c = gam[c-1] W_c: scale of each stored (unnormalised) basis vector
-    double coef[130];   // beta gam_c u_c: coefficients of Fig. 2 line 23
+    double coef[130];   // beta gam_c u_c: coefficients of the Krylov combine (Fig. 2)
     double vmean[130];  // mean of each basis vector (mixed-precision mass correction)
     double resj[130];   // resnorm(tau0) of Krylov dimension j (block-parallel phi)
     unsigned int ticket[8];
@@ -266,13 +266,13 @@ void launch_energy(const Launch &L, const Geom &g, const double *y);
 void launch_krylov_arm(const Launch &L, double tau0, double tol_phi_fixed, double tol,
                        int use_ghat);
 
-// Projected phi, residual test and step trace of Fig. 2 lines 9-20 (ch_phi.cu)
+// Projected phi, residual test and step trace of Fig. 2 (ch_phi.cu)
 int phi_setup();
 void launch_phi(const Launch &L, double *H, int ldh, int j, int mmax, double *u,
                 double *scratch);
-// Block-parallel projected phi for Krylov dimensions j0..j1 (Fig. 2 lines 10-14 for each j
+// Block-parallel projected phi for Krylov dimensions j0..j1 (Fig. 2, projected phi and residual test for each j
 // from the same H), then the decision: the first j whose residual test passes ends the run;
-// with none and j1 == mmax the step trace of lines 15-19 runs at mmax.
+// with none and j1 == mmax the step trace of Fig. 2 runs at mmax.
 void launch_phi_block(const Launch &L, double *H, int ldh, int j0, int j1, int mmax, double *u,
                       double *ub, int ldu);
 // Batched projected phi: one 8-CTA cluster per instance, j + 1 <= 64.

@@ -1,5 +1,5 @@
 // ch_phi.cu -- projected phi evaluation, residual test and residual-time step choice of the
-// Krylov method of Fig. 2 (lines 9-20), in FP64 on one thread block.
+// Krylov method of Fig. 2, in FP64 on one thread block.
 //
 // u = s phi(-s H_j) e_1 (Eqs. phi, yt_m) is the last column of exp([[-s H_j, s e_1], [0, 0]]).
 // The exponential uses the diagonal Pade approximant of degree 13 with scaling and squaring
@@ -19,7 +19,7 @@ namespace ch {
 constexpr int kPhiThreads = 512;
 constexpr int kPhiCluster = 8;     // CTAs of the cluster that shares the matrix products
 constexpr int kPhiSmemMaxN = 64;
-constexpr int kMaxHalvings = 60;   // fixed trace rule of Fig. 2 lines 16-17
+constexpr int kMaxHalvings = 60;   // fixed rule for the step trace of Fig. 2
 constexpr int kBisections = 12;
 
 constexpr int kTraceSlots = kBisections + 1;   // exp(M(lo0 / 2^b)), b = 0..12
@@ -175,7 +175,7 @@ __device__ double *expm_block(int n, PhiWork &W, const MM &mm) {
         __syncthreads();
     }
     double *R = Q, *S = X6;
-    // R = exp(M / 2^sq); record its (n-2, n-1) entry (the residual entry of Fig. 2 line 12)
+    // R = exp(M / 2^sq); record its (n-2, n-1) entry (the residual entry of Fig. 2)
     // for s / 2^sq, then after each squaring for s / 2^(sq-k-1)
     if (threadIdx.x == 0) {
         W.sq = sq;
@@ -191,7 +191,7 @@ __device__ double *expm_block(int n, PhiWork &W, const MM &mm) {
 }
 
 // u = s phi(-s H_j) e_1 (written to `u` when u != nullptr, else kept in W.fcol); returns
-// resnorm = h_{j+1,j} |e_j^T u| (Fig. 2 line 12).
+// resnorm = h_{j+1,j} |e_j^T u| (Fig. 2).
 template <typename MM>
 __device__ double phi_eval(int j, const double *H, int ldh, double hnext, double s, double *u,
                            PhiWork &W, const MM &mm) {
@@ -210,10 +210,10 @@ __device__ double phi_eval(int j, const double *H, int ldh, double hnext, double
     if (u)
         for (int r = threadIdx.x; r < j; r += blockDim.x) u[r] = E[r * n + j];
     __syncthreads();
-    return hnext * fabs(last);                          // Fig. 2 line 12
+    return hnext * fabs(last);                          // resnorm of Fig. 2
 }
 
-// Fig. 2 lines 9-20 for iteration j, on one CTA (MM = MatmulBlock) or one cluster (every
+// Fig. 2 after the Arnoldi process, for iteration j, on one CTA (MM = MatmulBlock) or one cluster (every
 // CTA runs the same control flow on identical data; rank 0 alone writes results).
 template <typename MM>
 __device__ void phi_step(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double *u,
@@ -234,19 +234,19 @@ __device__ void phi_step(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double
             W.c[k] = W.c[k - 1] * (double)(13 - k + 1) / ((double)(2 * 13 - k + 1) * k);
     }
     __syncthreads();
-    const double hnext = H[j * ldh + (j - 1)];           // Fig. 2 line 9 (last MGS pass)
+    const double hnext = H[j * ldh + (j - 1)];           // h_{j+1,j} (last MGS pass)
     const double tau0 = ctrl->tau0, tol = ctrl->tol_phi;
     double *uo = writer ? u : nullptr;
     int evals = 1;
-    double res = phi_eval(j, H, ldh, hnext, tau0, uo, W, mm);  // lines 10-12
+    double res = phi_eval(j, H, ldh, hnext, tau0, uo, W, mm);  // phi and resnorm at tau0
     int done = 0, shrunk = 0, status = 0;
     double tau = tau0;
     if (!isfinite(hnext) || !isfinite(res)) {
         status = CH_ENONFINITE;
         done = 1;
-    } else if (res <= tol) {                                // lines 13-14
+    } else if (res <= tol) {                                // converged
         done = 1;
-    } else if (j == mmax) {                                 // lines 15-19
+    } else if (j == mmax) {                                 // step trace
         // Halve s from tau0 until resnorm(s) <= tol_phi: the trials s = tau0/2^k with
         // k <= sq are the intermediate squarings of the evaluation at tau0 (same arithmetic
         // as a fresh evaluation, whose scaling exponent is sq - k), recorded in W.chain.
@@ -292,7 +292,7 @@ __device__ void phi_step(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double
                     lo += ldexp(lo0, -b);
                 }
             }
-            if (uo)                                      // line 18: u = s phi(-s H) e_1 at s = lo
+            if (uo)                                      // u = s phi(-s H) e_1 at s = lo
                 for (int r = threadIdx.x; r < j; r += blockDim.x) uo[r] = W.cur[r * n + j];
             __syncthreads();
             tau = lo;
@@ -306,7 +306,7 @@ __device__ void phi_step(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double
                 else hi = mid;
             }
             ++evals;
-            phi_eval(j, H, ldh, hnext, lo, uo, W, mm);      // line 18
+            phi_eval(j, H, ldh, hnext, lo, uo, W, mm);      // u at s = lo
             tau = lo;
             shrunk = 1;
         }
@@ -329,12 +329,12 @@ __device__ void phi_step(Ctrl *ctrl, double *H, int ldh, int j, int mmax, double
                 ctrl->shrunk = shrunk;
             }
         } else {
-            ctrl->gam[j] = 1.0 / hnext;                      // v_{j+1} = w / h_{j+1,j}, line 21
+            ctrl->gam[j] = 1.0 / hnext;                      // v_{j+1} = w / h_{j+1,j}
         }
     }
     if (done && !status)
         for (int c = threadIdx.x; c < j; c += blockDim.x)
-            ctrl->coef[c] = ctrl->beta * ctrl->gam[c] * u[c];   // line 23
+            ctrl->coef[c] = ctrl->beta * ctrl->gam[c] * u[c];   // Krylov combine
 }
 
 __global__ void __launch_bounds__(kPhiThreads)
@@ -409,7 +409,7 @@ k_phi_multi_block(Ctrl *ctrl, const double *H, int ldh, int j0, double *ub, int 
                   MatmulBlock());
 }
 
-// First j in [j0, jlast] whose residual test passed (Fig. 2 lines 13-14): that j ends the
+// First j in [j0, jlast] whose residual test passed (Fig. 2): that j ends the
 // run, exactly as the per-iteration test would; a non-finite residual first ends it with an
 // error.  Returns true when the run ended.
 __device__ bool decide_first(Ctrl *ctrl, int j0, int jlast, const double *ub, int ldu,
@@ -443,7 +443,7 @@ __device__ bool decide_first(Ctrl *ctrl, int j0, int jlast, const double *ub, in
         }
         if (d > 0)
             for (int c = threadIdx.x; c < d; c += blockDim.x)
-                ctrl->coef[c] = ctrl->beta * ctrl->gam[c] * ub[(size_t)(d - j0) * ldu + c];  // line 23
+                ctrl->coef[c] = ctrl->beta * ctrl->gam[c] * ub[(size_t)(d - j0) * ldu + c];  // Krylov combine
     }
     __syncthreads();
     return true;

@@ -7,7 +7,7 @@
 //   stage 2:                                 w = c0 t - sum_a c_a (t_{+a} + t_{-a})
 // With D = 3 y^2 - 1 [+1 Eyre] + eps^2 sigma, kap_a = eps^2 s_a, c0 = sigma, c_a = s_a this
 // is A_hat v = A (J + eps^2 A [+ I]) v of Eqs. (A_g), (A_g_cs); other coefficient choices
-// give f(y) of Eq. (IVP), the LIM residual g_hat - A_hat y (Fig. 1 steps 6/10) and the PC
+// give f(y) of Eq. (IVP), the LIM residual g_hat - A_hat y (Fig. 1) and the PC
 // estimate of Eq. (LIMest).  Neighbour indices wrap periodically.
 #include <math.h>
 
@@ -156,7 +156,7 @@ template <> struct DotAcc<float> {
 // Per-step preparation from the linearisation point y^n:
 //   D = 3 y^2 - 1 (+1 Eyre) + eps^2 sigma   (diagonal of J_n + eps^2 A [+I] before -kap sums)
 //   G = 2 y^3 (+ y Eyre)                    (= J_n y - F'(y) [+ y], inner part of g_hat)
-//   min / max of y^2                        (Fig. 1 step 1: lambda_max from d_min, d_max)
+//   min / max of y^2                        (bound of Fig. 1: lambda_max from d_min, d_max)
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads)
 k_prep(Geom g, const double *__restrict__ y, double dconst, int eyre, double *__restrict__ D,
@@ -197,10 +197,10 @@ k_prep(Geom g, const double *__restrict__ y, double dconst, int eyre, double *__
 }
 
 // ---------------------------------------------------------------------------------------
-// Arnoldi matvec (Fig. 2 line 4) on the unnormalised basis vector x = W_j (v_j = gam_j W_j):
+// Arnoldi product of Fig. 2 on the unnormalised basis vector x = W_j (v_j = gam_j W_j):
 //   tstage: t = D (.) x - sum_a kap_a (x_{+a} + x_{-a})
 //   wstage: w = gam_j (sigma t - sum_a s_a (t_{+a} + t_{-a}))  = A_hat v_j
-//           and h_{1j} = w . v_1 = gam_1 (w . W_1)           (first pass of lines 5-8)
+//           and h_{1j} = w . v_1 = gam_1 (w . W_1)           (first Gram-Schmidt pass)
 // ---------------------------------------------------------------------------------------
 template <int DIM, typename VT>
 __global__ void __launch_bounds__(kThreads)
@@ -233,9 +233,9 @@ k_wstage(Geom g, const VT *__restrict__ t, VT *__restrict__ w, const VT *__restr
 }
 
 // ---------------------------------------------------------------------------------------
-// Modified Gram-Schmidt pass k of Fig. 2 lines 5-8, fused with the next dot product:
+// Modified Gram-Schmidt pass k of Fig. 2, fused with the next dot product:
 //   w -= h_{kj} v_k  (= h_{kj} gam_k W_k),  then  h_{k+1,j} = w . v_{k+1}   (k < j)
-//                                           or    ||w||^2 for line 9       (k = j)
+//                                           or    ||w||^2 for h_{j+1,j}    (k = j)
 // ---------------------------------------------------------------------------------------
 // 16-byte vectors of the basis precision: double2 / float4.
 template <typename VT> struct Vec16;
@@ -282,7 +282,7 @@ k_mgs(int64_t N, VT *__restrict__ w, const VT *__restrict__ vk, const VT *__rest
     double tot1[1] = {acc.value()};
     if (!last)
         grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { *hout = ctrl->gam[k] * tot[0]; });
-    else   // Fig. 2 lines 9 and 21: h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
+    else   // Fig. 2: h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
         grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) {
             ctrl->hnext2 = tot[0];
             const double h = sqrt(tot[0]);
@@ -292,7 +292,7 @@ k_mgs(int64_t N, VT *__restrict__ w, const VT *__restrict__ vk, const VT *__rest
 }
 
 // ---------------------------------------------------------------------------------------
-// One whole Arnoldi iteration j (Fig. 2 lines 4-9 and the scale of line 21) in one
+// One whole Arnoldi iteration j (Fig. 2, with the scale of v_{j+1}) in one
 // cooperative launch of one 1024-thread block per SM: t-stage, w-stage with h_{1j}, then
 // the j modified Gram-Schmidt passes, separated by grid barriers.  After each barrier every
 // block adds the per-block partials in block order itself (the same value in every block,
@@ -407,7 +407,7 @@ struct ArnShared {
 // End of round k + 1 (thread 0 has posted this block's partial): warp 0 waits at the grid
 // barrier and sums the partials, and in thread 0
 //   k < j:  h_{k+1,j} = gam_k sum (row k of H), next coefficient h_{k+1,j} gam_k;
-//   k = j:  h_{j+1,j} = sqrt(sum) (Fig. 2 line 9), gam_j = 1 / h_{j+1,j};
+//   k = j:  h_{j+1,j} = sqrt(sum) (Fig. 2), gam_j = 1 / h_{j+1,j};
 // k = 0 is the w-stage round: h_{1j} = gam_0 sum.  Block 0 writes H and the control block.
 template <typename VT>
 __device__ __forceinline__ void arn_finish_round(GridBarrier &gb, const double *part, int k, int j,
@@ -470,7 +470,7 @@ k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const
         if (threadIdx.x == 0) partials[G + blockIdx.x] = bsum;
     }
     arn_finish_round<VT>(gb, partials + G, 0, j, H, ldh, ctrl, &sc);     // h_{1j}
-    // ---- modified Gram-Schmidt passes k = 1..j (lines 5-8) and the norm of line 9
+    // ---- modified Gram-Schmidt passes k = 1..j and the norm h_{j+1,j}
     for (int k = 1; k <= j; ++k) {
         const bool last = (k == j);
         const VT c = sc.c;
@@ -571,7 +571,7 @@ k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
     VT *out = W(j + 1);
     // elements of this thread that exist (the rest of its slots hold zeros)
     const int Rn = i0 < N ? (int)min((unsigned)R, (N - i0 + S - 1) / S) : 0;
-    // ---- modified Gram-Schmidt passes k = 1..j (lines 5-8) and the norm of line 9;
+    // ---- modified Gram-Schmidt passes k = 1..j and the norm h_{j+1,j};
     //      odd passes update with buffer A and dot with B, even passes the other way round
     for (int k = 1; k <= j; ++k) {
         const bool last = (k == j);
@@ -609,7 +609,7 @@ k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
 // ---------------------------------------------------------------------------------------
 // Arnoldi iteration j for an FP32 basis with Gram-corrected modified Gram-Schmidt.
 //
-// Fig. 2 lines 5-8 give h_kj = v_k . w^(k-1) with w^(k-1) = w - sum_{i<k} h_ij v_i, i.e.
+// Fig. 2's modified Gram-Schmidt gives h_kj = v_k . w^(k-1) with w^(k-1) = w - sum_{i<k} h_ij v_i, i.e.
 //     h_kj = c_k - sum_{i<k} G_ki h_ij,   c_k = v_k . w,   G_ki = v_k . v_i   (i < k),
 // an identity for any computed basis, so these are the modified Gram-Schmidt coefficients
 // (not classical Gram-Schmidt, which drops the G terms).  All c_k, and the Gram row of the
@@ -1005,7 +1005,7 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         const double nrm2 = gs_grid_sum_warp(pB, 0);
         if (threadIdx.x == 0) {
-            const double hn = sqrt(nrm2);                         // h_{j+1,j} (Fig. 2 line 9)
+            const double hn = sqrt(nrm2);                         // h_{j+1,j} (Fig. 2)
             ctrl->hnext2 = nrm2;
             H[j * ldh + (j - 1)] = hn;
             ctrl->gam[j] = 1.0 / hn;
@@ -1109,7 +1109,7 @@ template void launch_arnoldi<float>(const Launch &, int, const Geom &, float *, 
                                     const float *, float *, double *, int, int);
 
 // ---------------------------------------------------------------------------------------
-// Fig. 2 line 23: y_next = y0 + V_j (beta u) = y0 + sum_c coef_c W_c, coef_c = beta gam_c u_c.
+// Krylov combine of Fig. 2: y_next = y0 + V_j (beta u) = y0 + sum_c coef_c W_c, coef_c = beta gam_c u_c.
 // Column 0 is `v0`, columns 1.. start at V with stride ldv.
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads)
@@ -1239,8 +1239,8 @@ k_rhs2(Geom g, const double *__restrict__ mu, const double *__restrict__ q,
 }
 
 // ---------------------------------------------------------------------------------------
-// Residual of the linearised implicit Euler system, r = g_hat - A_hat x  (Fig. 1 steps 6/10,
-// and Fig. 2 line 2 for a restart from x = y_cur):
+// Residual of the linearised implicit Euler system, r = g_hat - A_hat x  (the LIM update of Fig. 1,
+// and the start vector of Fig. 2 for a restart from x = y_cur):
 //   resid1: t = G - D (.) x + sum_a kap_a (x_{+a} + x_{-a})
 //   resid2: r = sigma t - sum_a s_a (t_{+a} + t_{-a}),  ||r||^2 -> red[0]
 //   lim2:   y_next = (y^n + tau a_m y_prev + tau r) / (1 + tau a_m)
@@ -1330,7 +1330,7 @@ k_energy(Geom g, const double *__restrict__ y, double *partials, unsigned int *t
 }
 
 // ---------------------------------------------------------------------------------------
-// Krylov start (Fig. 2 line 2) from the norms left in red[] by rhs2 / resid2:
+// Krylov start (the start vector of Fig. 2) from the norms left in red[] by rhs2 / resid2:
 // beta = ||W_1||, gam_1 = 1/beta; tol_phi by Eq. (tol_phi) unless fixed (> 0).
 // beta == 0 (stationary linear IVP) leaves the run inactive with jexit = 0, y_next = y0.
 // ---------------------------------------------------------------------------------------

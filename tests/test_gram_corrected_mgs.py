@@ -1,5 +1,5 @@
 """The identity behind the FP32 Arnoldi iteration: for any computed (not exactly orthonormal)
-basis v_1..v_j, the modified Gram-Schmidt coefficients of Fig. 2 lines 5-8,
+basis v_1..v_j, the modified Gram-Schmidt coefficients of Fig. 2,
     h_k = v_k . (w - sum_{i<k} h_i v_i),
 equal the forward substitution h_k = c_k - sum_{i<k} G_ki h_i with c_k = v_k . w and the
 Gram matrix G_ki = v_k . v_i.  Checked in FP64 on bases with a controlled loss of

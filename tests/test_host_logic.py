@@ -1,11 +1,11 @@
 """Host-side logic of the CUDA library, run without a GPU through its host-only C calls and
 compared with the oracle:
 
-* ch_lim_schedule (Fig. 1 steps 1, 2, 5 as the GPU path runs them): p equals the oracle's
+* ch_lim_schedule (p, parameter order and a_m of Fig. 1 as the GPU path uses them): p equals the oracle's
   Eq. (p), the parameter order equals the oracle's, and the schedule applied to scalar
   modes mu in [0, lambda_max] (the step y <- (y + tau a_m y - tau mu y) / (1 + tau a_m)
-  of Fig. 1, steps 6 and 10) reproduces the oracle's LIM step on the 1 x 1 problem.
-* ch_lambda_max_bound (Fig. 1 step 1 in the closed form the GPU uses) equals the oracle's
+  of Fig. 1) reproduces the oracle's LIM step on the 1 x 1 problem.
+* ch_lambda_max_bound (the spectral bound of Fig. 1 in the closed form the GPU uses) equals the oracle's
   ||A_hat||_1 formed column by column.
 """
 import ctypes

@@ -83,7 +83,7 @@ def test_lim_is_first_order(oracle):
 
 
 def test_adaptive_controllers_follow_eq_eedt_and_eq_limdt(oracle):
-    """Figs. 3/4 step 10 from the recorded (tau, est): EE2 tau_new = min(5/4 tau,
+    """The step-size update of Figs. 3/4 from the recorded (tau, est): EE2 tau_new = min(5/4 tau,
     sqrt(tol/est) tau) (Eq. EEdt); LIM tau_new = tol/est tau (Eq. LIMdt); the last step ends at T."""
     n = (24, 24); T = 1e-4; tol = 1e-5
     g = oracle.Grid(2, n, 0.03)

@@ -96,7 +96,7 @@ def test_krylov_step_equals_augmented_expm(oracle, tau):
 
 
 def test_krylov_shrinks_step_and_meets_tolerance(oracle):
-    """Fig. 2 lines 15-19: at j = m_max the step is cut to an admissible tau < tau0 and the
+    """Fig. 2, step trace: at j = m_max the step is cut to an admissible tau < tau0 and the
     Krylov solution then satisfies Eq. (phi_stop) against the exact linear solution."""
     y, M, g = _ch_dense()
     N = M.shape[0]

@@ -11,7 +11,7 @@ from paper_2502_14589_gb300 import inputs
 
 
 def nodes(p, lmax):
-    """a_m of Fig. 1 steps 2-5 (natural order)."""
+    """a_m of Fig. 1 (natural order)."""
     beta = np.cos(np.pi * (2 * np.arange(1, p + 1) - 1) / (2 * p))
     z1 = beta[0]
     return lmax / (1 + z1) * (z1 - beta)
@@ -112,7 +112,7 @@ def _growth_times_tail(p, X, order, npts):
 
 @pytest.mark.parametrize("p", [1, 2, 3, 5, 8, 21, 40, 64, 125])
 def test_lim_order_keeps_roundoff_growth_near_square_of_tau_lambda(oracle, p):
-    """Fig. 1 step 2: the order starts with beta_1 and is a permutation; its rounding-error
+    """Fig. 1, ordered set: the order starts with beta_1 and is a permutation; its rounding-error
     growth stays within 3 (tau lambda_max)^2, whereas the natural order exceeds 1e13 at
     p = 21 and overflows double precision beyond p ~ 150."""
     order = oracle.lim_order(p)

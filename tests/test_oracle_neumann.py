@@ -91,8 +91,8 @@ def test_neumann_rhs_by_cosine_transform(oracle, dim, n):
 @pytest.mark.parametrize("dim,n", GRIDS)
 @pytest.mark.parametrize("eyre", [False, True])
 def test_neumann_jacobian_and_one_norm(oracle, dim, n, eyre):
-    """Eqs. (A_g) / (A_g_cs) against the dense A_hat; g_hat - A_hat y = f; Fig. 1 step 1
-    lambda_max = ||A_hat||_1 against the dense column sums."""
+    """Eqs. (A_g) / (A_g_cs) against the dense A_hat; g_hat - A_hat y = f; the bound of
+    Fig. 1, lambda_max = ||A_hat||_1 against the dense column sums."""
     eps = 0.06
     g = oracle.Grid(dim, n, eps, eyre=eyre, bc="neumann")
     y = inputs.initial_state(n, 11, -0.9, 0.9)

@@ -1,5 +1,5 @@
 """Pins of the oracle's spatial operators (Sec. 2 Eq. IVP; Sec. 3 Eqs. A_g, J, A_g_cs, p;
-Fig. 1 step 1) against Fourier symbols, dense matrices, finite differences and the LIM
+the spectral bound of Fig. 1) against Fourier symbols, dense matrices, finite differences and the LIM
 matvec counts the paper prints in Tables 1 and 2."""
 import os
 
@@ -77,7 +77,7 @@ def test_ghat_minus_Ahat_y_is_rhs(oracle, dim, n, eyre):
                                    (3, (3, 4, 5)), (3, (5, 5, 5)), (3, (6, 5, 7))])
 @pytest.mark.parametrize("eyre", [False, True])
 def test_lambda_max_is_dense_one_norm(oracle, dim, n, eyre):
-    """Fig. 1 step 1: lambda_max = max_j sum_i |a_ij|, also on grids whose +-2 offsets alias."""
+    """Fig. 1, spectral bound: lambda_max = max_j sum_i |a_ij|, also on grids whose +-2 offsets alias."""
     eps = 0.07
     g = oracle.Grid(dim, n, eps, eyre=eyre)
     y = inputs.initial_state(n, 21, -1.1, 1.1)
@@ -88,7 +88,7 @@ def test_lambda_max_is_dense_one_norm(oracle, dim, n, eyre):
 
 @pytest.mark.parametrize("dim,n", [(2, (6, 5)), (3, (4, 5, 6))])
 def test_column_abs_sum_is_dense_column_sum(oracle, dim, n):
-    """One column of Fig. 1 step 1: the absolute sum of every column of A_hat."""
+    """One column of the bound of Fig. 1: the absolute sum of every column of A_hat."""
     eps = 0.07
     g = oracle.Grid(dim, n, eps)
     y = inputs.initial_state(n, 22, -1.1, 1.1)
@@ -111,7 +111,7 @@ def _golden_counts():
 @pytest.mark.parametrize("row", _golden_counts(), ids=lambda r: f"n{r[0]}-tau{r[1]}-eyre{r[2]}")
 def test_lim_matvec_counts_printed_in_paper(oracle, row):
     """Tables 1 and 2 (LIM columns): T/tau steps of 2p-1 matvecs with p from Eq. (p) and
-    lambda_max from Fig. 1 step 1.  The paper's domain (0,64)^2 with h = 64/n is mapped to the
+    lambda_max = ||A_hat||_1 (Fig. 1).  The paper's domain (0,64)^2 with h = 64/n is mapped to the
     unit square by x' = x/64, t' = t/64^2, eps' = eps/64, which leaves tau*lambda_max fixed."""
     n, tau, eyre, printed, kind = row
     eps4 = 1.0 * 4 / (2 * np.sqrt(2) * np.arctanh(0.9))     # Eq. (eps), h = 1, m = 4
