@@ -20,9 +20,9 @@
  * Readings of points where the paper is silent:
  *  - periodic boundary conditions for the benchmark workloads; the paper's Neumann
  *    conditions are the other choice of or_grid.bc;
- *  - "trace resnorm for s in [0,tau0]" (Fig. 2, RT algorithm) = halve s from the upper
- *    end until the residual test passes, then bisect a fixed number of times keeping
- *    the admissible end;
+ *  - the residual trace over s in [0, tau0] of Fig. 2 (left unspecified) = halve s from
+ *    the upper end until the residual test passes, then bisect a fixed number of times
+ *    keeping the admissible end;
  *  - constant-step EE2 uses linear residual-time restarting over the whole step with
  *    A_hat, g_hat frozen at y^n;
  *  - the order of beta_2..beta_p (left open by Fig. 1) bounds round-off growth (or_lim_order);
@@ -427,7 +427,7 @@ static double dot(long N, const double *a, const double *b) {
     return acc;
 }
 
-/* Fixed search rule for the step trace of Fig. 2 ("trace resnorm for s in [0, tau0]"):
+/* Fixed search rule for the step trace of Fig. 2 (the residual as a function of s in [0, tau0]):
  * halve s from s_max until resnorm(s) <= tol, at most OR_MAX_HALVINGS times, then
  * OR_BISECTIONS bisection steps between that admissible s and the last rejected one,
  * keeping the admissible end.                                                           */
