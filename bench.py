@@ -244,11 +244,11 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
     if world > 1:
-        import torch.distributed as dist
+        from paper_2502_14589_gb300 import replicas
         if args.impl == "gb300":                 # the reference arm runs on the host only
             import torch
             torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
+        dist = replicas.init_process_group("nccl" if args.impl == "gb300" else "gloo")
     if args.impl == "reference":
         run_reference(args, rank, world)
         if dist is not None:

@@ -9,6 +9,17 @@ slowest rank's time.  Works with any torch.distributed backend (NCCL on GPUs, gl
 from __future__ import annotations
 
 
+def init_process_group(backend: str, timeout_s: float = 600.0):
+    """Join the job's process group (RANK, WORLD_SIZE, MASTER_ADDR/PORT from the environment)
+    with a bounded wait: when a rank fails or never arrives, the next collective of the
+    others ends with an error after at most `timeout_s` seconds instead of waiting forever."""
+    import datetime
+
+    import torch.distributed as dist
+    dist.init_process_group(backend, timeout=datetime.timedelta(seconds=float(timeout_s)))
+    return dist
+
+
 def instance_seed(rank: int) -> int:
     """Seed of the initial state integrated by `rank` (rank 0 runs the seed-0 workload)."""
     return int(rank)
