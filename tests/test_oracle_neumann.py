@@ -186,3 +186,69 @@ def test_lim_counts_on_the_papers_neumann_grid(oracle, row):
     else:
         assert min(counts) <= printed <= max(counts)
 
+
+
+def _dense_neumann_ahat(n, y, eps, eyre):
+    A = dense_neumann_A(n)
+    return A @ (np.diag(3 * y ** 2 - 1 + (1.0 if eyre else 0.0)) + eps ** 2 * A), A
+
+
+@pytest.mark.parametrize("eyre", [False, True])
+def test_neumann_lim_step_equals_dense_lim(oracle, eyre):
+    """Fig. 1 on the Neumann grid equals the LIM core on the dense A_hat, g_hat, ||A_hat||_1."""
+    n = (7, 6); eps = 0.06
+    g = oracle.Grid(2, n, eps, eyre=eyre, bc="neumann")
+    y = inputs.initial_state(n, 9, -0.9, 0.9)
+    M, A = _dense_neumann_ahat(n, y, eps, eyre)
+    gv = A @ (2 * y ** 3 + (y if eyre else 0.0))
+    lmax = np.abs(M).sum(axis=0).max()
+    tau = 37.0 / lmax
+    out, p, lm, mv = oracle.lim_step(g, y, tau)
+    ref, p2 = oracle.lim_dense(M, gv, y, tau, lmax)
+    assert p == p2 and mv == 2 * p - 1
+    assert abs(lm - lmax) < 1e-13 * lmax
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("linear_restart,mmax", [(False, 30), (True, 5)])
+def test_neumann_ee_step_equals_augmented_exponential(oracle, linear_restart, mmax):
+    """Eq. (yt) on the Neumann grid: y^n + tau phi(-tau A_hat)(g_hat - A_hat y^n) from the
+    dense (N+1) x (N+1) augmented exponential, with and without linear restarting."""
+    import scipy.linalg
+    n = (6, 5); eps = 0.07
+    g = oracle.Grid(2, n, eps, bc="neumann")
+    y = inputs.initial_state(n, 2, -0.8, 0.8)
+    M, A = _dense_neumann_ahat(n, y, eps, False)
+    gv = A @ (2 * y ** 3)
+    N = M.shape[0]
+    tau = 2e-3 if linear_restart else 1e-4
+    aug = np.zeros((N + 1, N + 1)); aug[:N, :N] = -tau * M; aug[:N, N] = tau * (gv - M @ y)
+    exact = y + scipy.linalg.expm(aug)[:N, N]
+    rc, out, taken, j, st = oracle.ee_step(g, y, tau, tol_phi_fixed=1e-11, mmax=mmax,
+                                           linear_restart=linear_restart)
+    assert rc == 0 and taken == tau
+    if linear_restart:
+        assert st["restarts"] >= 1
+    assert np.linalg.norm(out - exact) <= 1e-8 * np.linalg.norm(exact)
+
+
+def test_neumann_jacobian_spectrum_follows_propositions_1_and_2(oracle):
+    """Sec. 3, Propositions 1 and 2 with the Neumann A (also symmetric positive
+    semidefinite): real eigenvalues equal to those of A^{1/2}(J + eps^2 A)A^{1/2}; only
+    nonnegative ones with the Eyre term."""
+    n = (6, 5); eps = 0.1
+    y = inputs.initial_state(n, 21, -0.6, 0.6)
+    A = dense_neumann_A(n)
+    lam, Q = np.linalg.eigh(A)
+    sqrtA = (Q * np.sqrt(np.clip(lam, 0.0, None))) @ Q.T
+    N = y.size
+    for eyre in (False, True):
+        g = oracle.Grid(2, n, eps, eyre=eyre, bc="neumann")
+        M = np.column_stack([oracle.jacvec(g, y, np.eye(N)[:, k]) for k in range(N)])
+        B = np.diag(3 * y ** 2 - 1 + (1.0 if eyre else 0.0)) + eps ** 2 * A
+        ev = np.linalg.eigvals(M)
+        scale = np.abs(ev).max()
+        assert np.abs(ev.imag).max() < 1e-9 * scale
+        assert np.abs(np.sort(ev.real) - np.linalg.eigvalsh(sqrtA @ B @ sqrtA)).max() < 1e-9 * scale
+        if eyre:
+            assert ev.real.min() > -1e-9 * scale
