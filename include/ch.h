@@ -185,7 +185,9 @@ ch_status ch_destroy_batch(ch_batch *b);
 /* offsets: count + 1 entries (last = total length of the concatenated array); chunk_len:
  * values per thread block picked by the creation-time tuner.  Either may be NULL.          */
 ch_status ch_batch_layout(const ch_batch *b, int64_t *offsets, int *chunk_len);
-/* prm: scheme CH_EE2, adaptive 1, no Eyre.  stats (optional) receives `count` entries.    */
+/* prm: scheme CH_EE2, adaptive 1, no Eyre.  stats (optional) receives `count` entries.
+ * When prm->max_steps batch steps pass before every instance reaches T, the call returns
+ * CH_ENOTCONV with y and stats holding the state reached (each instance's own t).         */
 ch_status ch_integrate_batch(ch_batch *b, const ch_params *prm, double *y, ch_stats *stats);
 int64_t ch_batch_kernel_launches(const ch_batch *b);
 

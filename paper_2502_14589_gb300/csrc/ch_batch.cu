@@ -637,6 +637,7 @@ ch_status integrate_b(ch_batch *b, const ch_params *prm, double *y, ch_stats *st
     rhs_b<VT>(b, s, ycur, cur, 0, nullptr, nullptr);                 // f(y^0), norms
     BCUDA(cudaGetLastError());
     int64_t steps = 0;
+    ch_status rc = CH_OK;
     for (;;) {
         kb_arm<<<(b->count + 255) / 256, 256, 0, s>>>(b->ctrls, b->bs, b->count, prm->T,
                                                       prm->tol_phi, prm->tol);
@@ -658,13 +659,15 @@ ch_status integrate_b(ch_batch *b, const ch_params *prm, double *y, ch_stats *st
         cur = 1 - cur;
         ++steps;
         if (b->hflags[2] == 0) break;
-        if (steps >= prm->max_steps) return bfail(CH_ENOTCONV, "max_steps reached before T");
+        if (steps >= prm->max_steps) {   // y and stats still receive the state reached
+            rc = bfail(CH_ENOTCONV, "max_steps reached before T");
+            break;
+        }
     }
     if (ycur != y) BCUDA(cudaMemcpyAsync(y, ycur, b->Ntot * sizeof(double), cudaMemcpyDeviceToDevice, s));
     std::vector<BState> hb(b->count);
     BCUDA(cudaMemcpyAsync(hb.data(), b->bs, b->count * sizeof(BState), cudaMemcpyDeviceToHost, s));
     BCUDA(cudaStreamSynchronize(s));
-    ch_status rc = CH_OK;
     for (int i = 0; i < b->count; ++i) {
         if (hb[i].status && rc == CH_OK)
             rc = bfail((ch_status)hb[i].status, "instance %d failed (status %d) at t = %g", i, hb[i].status, hb[i].t);
