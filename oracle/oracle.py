@@ -13,10 +13,12 @@ Parity status of each oracle routine (what pins it, see tests/test_oracle_*.py):
                                   at the Chebyshev nodes; stability on [0, lambda_max]; order 1
   expm, phi_e1                 -- scipy.linalg.expm, eigendecomposition, scalar closed form
   krylov / ee_step             -- dense augmented-matrix exponential of Eq. (yt); Arnoldi
-                                  relation; residual identity of Eq. (rm)
+                                  relation; residual identity of Eq. (rm); the EE2 matvec
+                                  counts printed in Tables 1-3 (paper's Neumann setting)
   estimate, drivers            -- mass conservation, energy decrease, Fourier linear decay,
-                                  convergence orders; the adaptive controller itself is
-                                  parity unpinned beyond its printed formulas
+                                  convergence orders; adaptive EE2 also by Table 3's work;
+                                  the adaptive LIM controller only by its printed formulas
+Planted mistakes in copies of ch_oracle.c (tests/test_oracle_mutants.py) each fail a pin.
 """
 from __future__ import annotations
 
