@@ -36,3 +36,23 @@ def test_reference_arm_prints_one_contract_line_from_rank_0():
     e2e = out["e2e"]
     assert e2e["value"] == out["value"] and e2e["unit"] == out["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_clock_samples_are_parsed_with_their_throttle_reasons():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    text = "\n".join([
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2040, 2070, 1399.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, [N/A], 2070, 10, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ])
+    c = bench.parse_clock_samples(text)
+    assert c["samples"] == 3 and c["sm_mhz"] == 2055.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    hot = bench.parse_clock_samples("0, 1500, 2070, 1400, 0x48, Not Active, Active, Not Active, Not Active")
+    assert hot["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.parse_clock_samples("")["sm_mhz"] is None
