@@ -27,7 +27,9 @@
  *    A_hat, g_hat frozen at y^n;
  *  - the order of beta_2..beta_p (left open by Fig. 1) bounds round-off growth (or_lim_order);
  *  - beta == 0 gives y^{n+1} = y^n; est == 0 keeps tau (LIM) or takes 5/4 tau (EE2);
- *  - a step clipped to end at T sets t := T exactly.
+ *  - a step clipped to end at T sets t := T exactly;
+ *  - variable mobility (the Remark on Eq. CHmob): conservative flux form with each face's
+ *    mobility the mean of its two nodes, nodal values supplied by the caller.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -42,6 +44,8 @@ typedef struct {
     double eps;     /* epsilon of the IVP (Sec. 2, Eq. IVP) */
     int eyre;       /* 0: A_hat, g_hat of Eq. (A_g); 1: Eyre splitting, Eq. (A_g_cs) */
     int bc;         /* 0: periodic; 1: homogeneous Neumann (Eq. CH), cell-centred nodes */
+    const double *mob; /* NULL: unit mobility (Eq. IVP); else the nodal mobility M(y^n_i) >= 0
+                          of Eq. (CHmob), frozen over the step as the Remark on it allows */
 } or_grid;
 
 typedef struct {            /* counters of work, as the paper counts it (Sec. 5.1) */
@@ -97,7 +101,28 @@ void or_apply_A(const or_grid *g, const double *v, double *out) {
     }
 }
 
-/* Eq. (F): F(c) = (1 - c^2)^2 / 4,  F'(c) = c (c^2 - 1). */
+/* The Remark on Eq. (CHmob): with a mobility M(c), the outer operator becomes A_M(y^n), a
+ * discretisation of -div(M grad .), frozen over the step.  Conservative flux form with the
+ * mobility of a cell face taken as the mean of its two nodes:
+ *   (A_M v)_i = sum_a (1/h_a^2) sum_{+-} (M_i + M_{i+-e_a})/2 (v_i - v_{i+-e_a}),
+ * symmetric, positive semidefinite for M >= 0, with zero column sums (mass).  A Neumann face
+ * has the node itself as its mirror neighbour, so its flux vanishes.  Unit mobility is A. */
+void or_apply_AM(const or_grid *g, const double *v, double *out) {
+    if (!g->mob) { or_apply_A(g, v, out); return; }
+    long N = or_N(g);
+    const double *M = g->mob;
+    for (long i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int a = 0; a < g->dim; ++a) {
+            double s = or_s(g, a);
+            long ip = shift(g, i, a, +1), im = shift(g, i, a, -1);
+            acc += s * (0.5 * (M[i] + M[ip]) * (v[i] - v[ip]) + 0.5 * (M[i] + M[im]) * (v[i] - v[im]));
+        }
+        out[i] = acc;
+    }
+}
+
+/* Eq. (F): F(c) = (1 - c^2)^2 / 4,  F'(c) = c (c^2 - 1). *//* Eq. (F): F(c) = (1 - c^2)^2 / 4,  F'(c) = c (c^2 - 1). */
 static double F(double c) { double t = 1.0 - c * c; return 0.25 * t * t; }
 static double Fp(double c) { return c * (c * c - 1.0); }
 
@@ -110,7 +135,7 @@ void or_rhs(const or_grid *g, const double *y, double *f) {
     double *Ay = malloc(N * sizeof(double)), *mu = malloc(N * sizeof(double));
     or_apply_A(g, y, Ay);
     for (long i = 0; i < N; ++i) mu[i] = Fp(y[i]) + g->eps * g->eps * Ay[i];
-    or_apply_A(g, mu, f);
+    or_apply_AM(g, mu, f);
     for (long i = 0; i < N; ++i) f[i] = -f[i];
     free(Ay); free(mu);
 }
@@ -124,7 +149,7 @@ void or_ghat(const or_grid *g, const double *yn, double *ghat) {
         t[i] = Jdiag(yn[i]) * yn[i] - Fp(yn[i]);
         if (g->eyre) t[i] += yn[i];
     }
-    or_apply_A(g, t, ghat);
+    or_apply_AM(g, t, ghat);
     free(t);
 }
 
@@ -138,7 +163,7 @@ void or_jacvec(const or_grid *g, const double *yn, const double *v, double *w) {
         t[i] = Jdiag(yn[i]) * v[i] + g->eps * g->eps * Av[i];
         if (g->eyre) t[i] += v[i];
     }
-    or_apply_A(g, t, w);
+    or_apply_AM(g, t, w);
     free(Av); free(t);
 }
 
@@ -172,16 +197,37 @@ static int sparse_apply_A(const or_grid *g, const or_entry *in, int nin, or_entr
     return cnt;
 }
 
+/* A_M applied to a sparse vector (column k of A_M for each input entry k; A_M is symmetric) */
+static int sparse_apply_AM(const or_grid *g, const or_entry *in, int nin, or_entry *out) {
+    if (!g->mob) return sparse_apply_A(g, in, nin, out);
+    const double *M = g->mob;
+    int cnt = 0;
+    for (int k = 0; k < nin; ++k) {
+        long c = in[k].idx;
+        for (int a = 0; a < g->dim; ++a) {
+            double s = or_s(g, a);
+            for (int off = -1; off <= 1; off += 2) {
+                long nb = shift(g, c, a, off);
+                double mf = 0.5 * (M[c] + M[nb]);
+                cnt = add_entry(out, cnt, c, s * mf * in[k].val);
+                cnt = add_entry(out, cnt, nb, -s * mf * in[k].val);
+            }
+        }
+    }
+    return cnt;
+}
+
 /* Absolute sum of column j of A_hat_n, formed explicitly. */
 double or_column_abs_sum(const or_grid *g, const double *yn, long j) {
-    or_entry e[1], Ae[8], AAe[64], col[64];
+    or_entry e[1], Ae[8], AAe[64], Me[8], col[64];
     double dj = Jdiag(yn[j]) + (g->eyre ? 1.0 : 0.0);
     e[0].idx = j; e[0].val = 1.0;
     int nA = sparse_apply_A(g, e, 1, Ae);          /* A e_j */
-    int nAA = sparse_apply_A(g, Ae, nA, AAe);      /* A A e_j */
-    /* column j of A_hat = A (D + eps^2 A) e_j = d_j A e_j + eps^2 A A e_j */
+    int nAA = sparse_apply_AM(g, Ae, nA, AAe);     /* A_M A e_j (A A e_j at unit mobility) */
+    int nM = sparse_apply_AM(g, e, 1, Me);         /* A_M e_j */
+    /* column j of A_hat = A_M (D + eps^2 A) e_j = d_j A_M e_j + eps^2 A_M A e_j */
     int nc = 0;
-    for (int k = 0; k < nA; ++k) nc = add_entry(col, nc, Ae[k].idx, dj * Ae[k].val);
+    for (int k = 0; k < nM; ++k) nc = add_entry(col, nc, Me[k].idx, dj * Me[k].val);
     for (int k = 0; k < nAA; ++k)
         nc = add_entry(col, nc, AAe[k].idx, g->eps * g->eps * AAe[k].val);
     double sum = 0.0;
@@ -616,7 +662,7 @@ double or_estimate(const or_grid *g, const double *yn, const double *ynp1, doubl
     for (long i = 0; i < N; ++i) sum[i] = yn[i] + ynp1[i];
     or_apply_A(g, sum, Asum);
     for (long i = 0; i < N; ++i) t[i] = Fp(yn[i]) + Fp(ynp1[i]) + g->eps * g->eps * Asum[i];
-    or_apply_A(g, t, Asum);
+    or_apply_AM(g, t, Asum);
     for (long i = 0; i < N; ++i) ypc[i] = yn[i] - 0.5 * tau * Asum[i];
     double num = 0.0, den = 0.0;
     for (long i = 0; i < N; ++i) {

@@ -6,7 +6,8 @@ library imports this module, and this module imports nothing from the library.
 
 Parity status of each oracle routine (what pins it, see tests/test_oracle_*.py):
   apply_A, rhs, ghat, jacvec   -- Fourier symbols (FFT), dense matrices, finite differences;
-                                  Neumann grids: cosine-transform symbols, dense matrices
+                                  Neumann grids: cosine-transform symbols, dense matrices;
+                                  variable mobility: dense flux-form matrices
   lambda_max, cheb_order       -- dense ||A_hat||_1 and the LIM matvec counts printed in
                                   Tables 1 and 2 of the paper
   lim_step                     -- p = 1 reduces to explicit Euler; exact implicit-Euler modes
@@ -50,7 +51,7 @@ def build(force: bool = False) -> str:
 
 class OrGrid(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_long * 3), ("eps", C.c_double), ("eyre", C.c_int),
-                ("bc", C.c_int)]
+                ("bc", C.c_int), ("mob", C.c_void_p)]
 
 
 class OrStats(C.Structure):
@@ -126,15 +127,23 @@ BCS = ("periodic", "neumann")
 
 class Grid:
     """Grid on the unit square (dim=2) or cube (dim=3), h_a = 1/n_a, with periodic
-    boundaries or the homogeneous Neumann conditions of Eq. (CH) on cell-centred nodes."""
+    boundaries or the homogeneous Neumann conditions of Eq. (CH) on cell-centred nodes.
+    `mobility`: None for unit mobility, else the nodal values M(y^n_i) >= 0 that make the
+    outer operator A_M of the Remark on Eq. (CHmob)."""
 
-    def __init__(self, dim: int, n, eps: float, eyre: bool = False, bc: str = "periodic"):
+    def __init__(self, dim: int, n, eps: float, eyre: bool = False, bc: str = "periodic",
+                 mobility=None):
         n = [int(n)] * dim if np.isscalar(n) else [int(v) for v in n]
         assert dim in (2, 3) and len(n) == dim and bc in BCS
         self.dim, self.n, self.eps, self.eyre, self.bc = dim, tuple(n), float(eps), bool(eyre), bc
         nn = (n + [1, 1])[:3]
-        self._g = OrGrid(dim, (C.c_long * 3)(*nn), float(eps), int(eyre), BCS.index(bc))
         self.N = int(np.prod(n))
+        self._mob = None
+        if mobility is not None:
+            self._mob = np.ascontiguousarray(mobility, dtype=np.float64).reshape(-1)
+            assert self._mob.size == self.N and np.all(self._mob >= 0.0)
+        self._g = OrGrid(dim, (C.c_long * 3)(*nn), float(eps), int(eyre), BCS.index(bc),
+                         None if self._mob is None else self._mob.ctypes.data)
 
     @property
     def shape(self):  # numpy shape, x fastest

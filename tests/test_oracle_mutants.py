@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ch_oracle.c")
 PINS = [os.path.join(ROOT, "tests", f) for f in
         ("test_oracle_operators.py", "test_oracle_krylov.py", "test_oracle_lim.py",
-         "test_oracle_drivers.py", "test_oracle_neumann.py")]
+         "test_oracle_drivers.py", "test_oracle_neumann.py", "test_oracle_mobility.py")]
 
 # (name, original text, planted text): the original must occur exactly once in ch_oracle.c
 MUTANTS = [
@@ -27,7 +27,7 @@ MUTANTS = [
      "mu[i] = Fp(y[i]) + g->eps * Ay[i];"),
     ("g_hat: Eyre term dropped", "if (g->eyre) t[i] += yn[i];", "if (g->eyre) t[i] += 0.0;"),
     ("A_hat: Eyre term sign", "if (g->eyre) t[i] += v[i];", "if (g->eyre) t[i] -= v[i];"),
-    ("lambda_max: |d_j| in the column", "dj * Ae[k].val", "fabs(dj) * Ae[k].val"),
+    ("lambda_max: |d_j| in the column", "dj * Me[k].val", "fabs(dj) * Me[k].val"),
     ("Eq. p: sqrt dropped", "atan(sqrt(tau * lambda_max))", "atan(tau * lambda_max)"),
     ("Fig. 1: sign of beta_m in a_m", "(z1 - beta[m - 1])", "(z1 + beta[m - 1])"),
     ("Fig. 1: y^n for y^(prev)", "tau * am * prev[i] +", "tau * am * yn[i] +"),
@@ -54,6 +54,14 @@ MUTANTS = [
      "if (i < 0) return -i;"),
     ("Neumann: vertex-centred mirror at the high face", "if (i >= n) return 2 * n - i - 1;",
      "if (i >= n) return 2 * n - i - 2;"),
+    ("mobility: upwind face value instead of the mean",
+     "0.5 * (M[i] + M[ip]) * (v[i] - v[ip])", "M[ip] * (v[i] - v[ip])"),
+    ("mobility: one-sided face value in the column sums", "double mf = 0.5 * (M[c] + M[nb]);",
+     "double mf = M[c];"),
+    ("mobility: plain A in the estimate's outer product", "    or_apply_AM(g, t, Asum);",
+     "    or_apply_A(g, t, Asum);"),
+    ("mobility: plain A as the outer operator of A_hat", "    or_apply_AM(g, t, w);",
+     "    or_apply_A(g, t, w);"),
     ("Neumann: periodic wrap kept", "i[a] = g->bc ? mirror(i[a] + off, g->n[a]) : wrap(i[a] + off, g->n[a]);",
      "i[a] = wrap(i[a] + off, g->n[a]);"),
 ]
