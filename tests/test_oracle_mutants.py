@@ -14,7 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ch_oracle.c")
 PINS = [os.path.join(ROOT, "tests", f) for f in
         ("test_oracle_operators.py", "test_oracle_krylov.py", "test_oracle_lim.py",
-         "test_oracle_drivers.py", "test_oracle_neumann.py", "test_oracle_mobility.py")]
+         "test_oracle_drivers.py", "test_oracle_neumann.py", "test_oracle_mobility.py",
+         "test_oracle_lim_controller.py")]
 
 # (name, original text, planted text): the original must occur exactly once in ch_oracle.c
 MUTANTS = [
@@ -48,6 +49,13 @@ MUTANTS = [
     ("Eq. EEdt: square root dropped", "sqrt(prm->tol / est) * taken", "(prm->tol / est) * taken"),
     ("Eq. LIMdt: square root added", "? (prm->tol / est) * taken : taken;",
      "? sqrt(prm->tol / est) * taken : taken;"),
+    ("Eq. LIMest: F'(y^n) twice in the corrector", "t[i] = Fp(yn[i]) + Fp(ynp1[i]) + g->eps * g->eps * Asum[i];",
+     "t[i] = Fp(yn[i]) + Fp(yn[i]) + g->eps * g->eps * Asum[i];"),
+    ("Eq. LIMest: y^n twice in the eps^2 A sum", "sum[i] = yn[i] + ynp1[i];", "sum[i] = yn[i] + yn[i];"),
+    ("Fig. 3: next step scaled from tau0", "? (prm->tol / est) * taken : taken;",
+     "? (prm->tol / est) * prm->tau0 : taken;"),
+    ("Fig. 3: no clip to T", "if (t + tau > prm->T) { tau = prm->T - t; clipped = 1; }",
+     "if (0) { tau = prm->T - t; clipped = 1; }"),
     ("energy: gradient term doubled", "0.5 * g->eps * g->eps * sG", "g->eps * g->eps * sG"),
     ("mass: cell volume dropped", "return vol * s;", "return s;"),
     ("Neumann: vertex-centred mirror at the low face", "if (i < 0) return -i - 1;",
