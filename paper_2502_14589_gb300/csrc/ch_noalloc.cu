@@ -132,6 +132,19 @@ ch_status ch_energy_mass_noalloc(int dim, const int64_t n[3], double eps, const 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(CH_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CH_EINVAL, "device index %d not supported", dev);
+    // y and out must be memory of this device: a host pointer or another GPU's memory
+    // would be dereferenced by a kernel running here.
+    const struct { const void *p; const char *name; } bufs[2] = {{y, "y"}, {out, "out"}};
+    for (const auto &b : bufs) {
+        cudaPointerAttributes at;
+        e = cudaPointerGetAttributes(&at, b.p);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CH_EINVAL, "%s is not a CUDA pointer: %s", b.name, cudaGetErrorString(e));
+        }
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+            return fail(CH_EINVAL, "%s must be device memory of the current device %d", b.name, dev);
+    }
     double *scratch;
     {
         std::lock_guard<std::mutex> lock(g_mu);
