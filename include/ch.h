@@ -86,7 +86,37 @@ typedef struct {
  * work of this grid is queued.  Allocates all workspace.  *out receives the handle.     */
 ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
                          int mmax_capacity, void *cuda_stream, ch_grid **out);
+
+/* Boundary conditions of a grid.  CH_BC_NEUMANN: the homogeneous Neumann conditions of
+ * Eq. (CH) on cell-centred nodes (Sec. 5.1, x_i = (i - 1/2) h_a), where the neighbour beyond
+ * a boundary face is the mirror image of the point inside, i.e. the point itself, so every
+ * difference across the boundary vanishes. */
+typedef enum { CH_BC_PERIODIC = 0, CH_BC_NEUMANN = 1 } ch_bc;
+
+typedef struct {
+    int bc;                 /* CH_BC_PERIODIC (default) or CH_BC_NEUMANN */
+    int variable_mobility;  /* 1: reserve the workspace of ch_set_mobility at creation */
+} ch_grid_options;
+
+/* ch_create_grid with options (NULL = periodic, unit mobility).  Same domain, spacing,
+ * precision modes and errors as ch_create_grid; CH_EINVAL for an unknown bc.            */
+ch_status ch_create_grid_ex(int dim, const int64_t n[3], double eps, int precision,
+                            int mmax_capacity, const ch_grid_options *opts, void *cuda_stream,
+                            ch_grid **out);
 ch_status ch_destroy_grid(ch_grid *g);
+
+/* The Remark on Eq. (CHmob): a variable mobility M(c) replaces the outer operator A by
+ * A_M(y^n), the flux form of -div(M grad .) frozen over a step:
+ *   (A_M t)_i = sum_a (1/h_a^2) sum_{+-} (M_i + M_{i+-e_a})/2 (t_i - t_{i+-e_a}),
+ * so A_hat = A_M (J + eps^2 A [+ I]), g_hat = A_M (J y - F'(y) [+ y]) and f = -A_M (F'(y) +
+ * eps^2 A y); the inner eps^2 A and the energy keep the constant-mobility Laplacian.  M is a
+ * caller-owned device array of N nodal values M_i >= 0 (for instance M(y^n_i) = 1 - (y^n_i)^2),
+ * read on the grid's stream before the call returns control of it; the face values are kept
+ * in the grid's workspace and used by every later call on the grid (rhs, jacvec,
+ * lambda_max, estimate, Krylov runs, EE2 / LIM steps, integrate) until the next
+ * ch_set_mobility.  To freeze the mobility at each step, call it before each step.  M = NULL
+ * restores unit mobility.  CH_EINVAL when the grid was not created with variable_mobility. */
+ch_status ch_set_mobility(ch_grid *g, const double *M);
 
 /* Sec. 2, Eq. (IVP): f = -A (F'(y) + eps^2 A y).  Optional host outputs: norm_f = ||f||_2
  * and norm_ghat = ||g_hat(y)||_2 with g_hat of Eq. (A_g) (or Eq. A_g_cs when `eyre`).     */
@@ -96,7 +126,9 @@ ch_status ch_rhs(ch_grid *g, const double *y, double *f, int eyre, double *norm_
 /* Eq. (A_g) / (A_g_cs): w = A_hat(y_lin) v = A (J + eps^2 A [+ I]) v.  Asynchronous.      */
 ch_status ch_jacvec(ch_grid *g, const double *y_lin, const double *v, double *w, int eyre);
 
-/* Fig. 1, spectral bound: lambda_max = ||A_hat(y)||_1 (host output, synchronises).       */
+/* Fig. 1, spectral bound: lambda_max = ||A_hat(y)||_1 (host output, synchronises).  Closed
+ * form from the extremes of y^2 on periodic constant-mobility grids, else the maximum of
+ * the explicitly formed column sums (Neumann boundaries, variable mobility).             */
 ch_status ch_lambda_max(ch_grid *g, const double *y, int eyre, double *lambda_max);
 
 /* Host-only (no GPU needed).  The spectral bound of Fig. 1 in the closed form the GPU path
@@ -259,9 +291,18 @@ ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us
  * unordered host threads) race and must be serialised by the caller.  The first call on each
  * device does a one-time set-up (it looks up the array's device address with
  * cudaGetSymbolAddress); make that first call before any stream capture.  Grids beyond
- * 2^31 - 1 points are rejected with CH_EINVAL.                                               */
+ * 2^31 - 1 points are rejected with CH_EINVAL, and so are y or out that are not device (or
+ * managed) memory of the current device, which is where the work runs; cuda_stream must
+ * belong to that device too.                                                                */
 ch_status ch_energy_mass_noalloc(int dim, const int64_t n[3], double eps, const double *y,
                                  double *out, void *cuda_stream);
+
+/* Measured FP64 FMA rate of the current GPU in TFLOP/s (an FMA counts 2): independent FMA
+ * chains from registers on a full grid, timed with CUDA events on cuda_stream (best of three
+ * launches after a warm-up).  No counterpart in the paper: it is the roofline denominator of
+ * the FP64 kernels, which are bound by FP64 issue on GB300.  Allocates and frees a small
+ * output buffer; synchronises the stream.                                                 */
+ch_status ch_probe_fp64_peak(void *cuda_stream, double *tflops);
 
 /* Message of the last error on the calling thread ("" when none). */
 const char *ch_last_error(void);

@@ -17,6 +17,8 @@ _LIB = None
 CH_OK, CH_EINVAL, CH_ENOMEM, CH_ECUDA, CH_ENOTCONV, CH_ENONFINITE, CH_ETIMEOUT = range(7)
 CH_FP64, CH_MIXED = 0, 1
 CH_EE2, CH_LIM = 0, 1
+CH_BC_PERIODIC, CH_BC_NEUMANN = 0, 1
+BCS = {"periodic": CH_BC_PERIODIC, "neumann": CH_BC_NEUMANN}
 STATUS_NAMES = {0: "CH_OK", 1: "CH_EINVAL", 2: "CH_ENOMEM", 3: "CH_ECUDA", 4: "CH_ENOTCONV",
                 5: "CH_ENONFINITE", 6: "CH_ETIMEOUT"}
 
@@ -31,6 +33,10 @@ class ch_params(C.Structure):
     _fields_ = [("scheme", C.c_int), ("adaptive", C.c_int), ("T", C.c_double),
                 ("tau0", C.c_double), ("tol", C.c_double), ("mmax", C.c_int),
                 ("tol_phi", C.c_double), ("eyre", C.c_int), ("max_steps", C.c_int64)]
+
+
+class ch_grid_options(C.Structure):
+    _fields_ = [("bc", C.c_int), ("variable_mobility", C.c_int)]
 
 
 class ch_stats(C.Structure):
@@ -49,6 +55,9 @@ _DP = C.POINTER(C.c_double)
 _IP = C.POINTER(C.c_int)
 _SIGS = {
     "ch_create_grid": [C.c_int, C.POINTER(C.c_int64), _D, C.c_int, C.c_int, _P, C.POINTER(_P)],
+    "ch_create_grid_ex": [C.c_int, C.POINTER(C.c_int64), _D, C.c_int, C.c_int, C.POINTER(ch_grid_options),
+                          _P, C.POINTER(_P)],
+    "ch_set_mobility": [_P, _P],
     "ch_destroy_grid": [_P],
     "ch_rhs": [_P, _P, _P, C.c_int, _DP, _DP],
     "ch_jacvec": [_P, _P, _P, _P, C.c_int],
@@ -74,6 +83,7 @@ _SIGS = {
     "ch_batch_layout": [_P, C.POINTER(C.c_int64), _IP],
     "ch_integrate_batch": [_P, C.POINTER(ch_params), _P, C.POINTER(ch_stats)],
     "ch_energy_mass_noalloc": [C.c_int, C.POINTER(C.c_int64), _D, _P, _P, _P],
+    "ch_probe_fp64_peak": [_P, _DP],
 }
 
 KERNEL_CLASSES = ["prep", "tstage", "wstage", "mgs", "phi", "combine", "rhs1", "rhs2",
@@ -158,6 +168,23 @@ def ch_create_grid(dim, n, eps, precision=CH_FP64, mmax_capacity=30, stream=None
     _check(load().ch_create_grid(dim, arr, eps, precision, mmax_capacity, _stream(stream), C.byref(h)))
     _register(h, nn[0] * nn[1] * nn[2])
     return h
+
+
+def ch_create_grid_ex(dim, n, eps, precision=CH_FP64, mmax_capacity=30, stream=None, bc="periodic",
+                      variable_mobility=False):
+    nn = list(n) + [1] * (3 - len(n))
+    arr = (C.c_int64 * 3)(*nn)
+    opts = ch_grid_options(BCS[bc] if isinstance(bc, str) else int(bc), int(bool(variable_mobility)))
+    h = C.c_void_p()
+    _check(load().ch_create_grid_ex(dim, arr, eps, precision, mmax_capacity, C.byref(opts), _stream(stream),
+                                    C.byref(h)))
+    _register(h, nn[0] * nn[1] * nn[2])
+    return h
+
+
+def ch_set_mobility(h, M):
+    """Nodal mobility M (device float64 tensor of N values, or None for unit mobility)."""
+    _check(load().ch_set_mobility(h, _vec(h, M)))
 
 
 def ch_destroy_grid(h):
@@ -307,13 +334,17 @@ def ch_timing_work(h):
 class Grid:
     """Owning handle around ch_create_grid / ch_destroy_grid."""
 
-    def __init__(self, dim, n, eps, precision=CH_FP64, mmax_capacity=30, stream=None):
+    def __init__(self, dim, n, eps, precision=CH_FP64, mmax_capacity=30, stream=None, bc="periodic",
+                 variable_mobility=False):
         n = [int(n)] * dim if isinstance(n, int) else [int(v) for v in n]
-        self.dim, self.n, self.eps = dim, tuple(n), eps
+        self.dim, self.n, self.eps, self.bc = dim, tuple(n), eps, bc
         self.N = 1
         for v in n:
             self.N *= v
-        self.h = ch_create_grid(dim, n, eps, precision, mmax_capacity, stream)
+        if bc == "periodic" and not variable_mobility:
+            self.h = ch_create_grid(dim, n, eps, precision, mmax_capacity, stream)
+        else:
+            self.h = ch_create_grid_ex(dim, n, eps, precision, mmax_capacity, stream, bc, variable_mobility)
 
     def close(self):
         if self.h is not None:
@@ -374,9 +405,24 @@ def ch_batch_kernel_launches(h):
 def ch_energy_mass_noalloc(dim, n, eps, y, out, stream=None):
     """Energy and mass of y into the device tensor out[0:2] without any allocation (queued on
     the stream, not synchronised); see include/ch.h for whom this entry point is for."""
+    import torch
     nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
-    if y is not None and y.numel() < nn[0] * nn[1] * nn[2]:
+    yp, op = _ptr(y), _ptr(out)
+    if y.numel() < nn[0] * nn[1] * nn[2]:
         raise ValueError(f"vector of {y.numel()} values; the grid has {nn[0] * nn[1] * nn[2]} points")
-    if out is not None and out.numel() < 2:
+    if out.numel() < 2:
         raise ValueError("out must hold 2 values")
-    _check(load().ch_energy_mass_noalloc(dim, nn, eps, _ptr(y), _ptr(out), _stream(stream)))
+    if out.device != y.device:
+        raise ValueError(f"y on {y.device} and out on {out.device}: both must be on one GPU")
+    if stream is not None and stream.device != y.device:
+        raise ValueError(f"stream of {stream.device}; y and out live on {y.device}")
+    # the C entry point works on the current device: make it the tensors' device
+    with torch.cuda.device(y.device):
+        _check(load().ch_energy_mass_noalloc(dim, nn, eps, yp, op, _stream(stream)))
+
+
+def ch_probe_fp64_peak(stream=None):
+    """Measured FP64 FMA rate of the current GPU (TFLOP/s, FMA = 2 flop)."""
+    out = C.c_double()
+    _check(load().ch_probe_fp64_peak(_stream(stream), C.byref(out)))
+    return out.value

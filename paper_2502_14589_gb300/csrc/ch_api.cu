@@ -77,6 +77,9 @@ struct ch_grid {
     int use_graphs;
     int fused_arnoldi;            // 1: one cooperative launch per Arnoldi iteration
     int arn_blocks;               // its grid
+    double *mfb[3];               // variable-mobility grids: face mobilities (FP64)
+    float *mffb[3];               // and their FP32 copies (mixed grids)
+    int var_mobility;             // 1: created with room for a variable mobility
     float2 *gpart;                // mixed grids: reduction scratch of the Gram-corrected iteration
     double *gram;                 // mixed grids: Gram matrix of the Krylov basis
     // device workspace
@@ -174,6 +177,22 @@ static double lambda_from_minmax(const Geom &G, double y2min, double y2max, int 
     return std::max(col_abs_sum(G, dmin), col_abs_sum(G, dmax));
 }
 
+// Fig. 1's spectral bound of A_hat(y), queued on the grid's stream: the closed form above
+// from the extremes of y^2 on periodic constant-mobility grids, else the maximum of the
+// explicit column sums (Neumann boundaries change the boundary columns, a variable mobility
+// every column).  lambda_read gives the value once the control block is on the host.
+static bool closed_form_bound(const Geom &G) { return G.bc == 0 && G.mf[0] == nullptr; }
+
+static void lambda_queue(ch_grid *g, const double *y, int eyre) {
+    if (closed_form_bound(g->g)) ch::launch_prep(g->L, g->g, y, eyre, g->D, nullptr, 1);
+    else ch::launch_colmax(g->L, g->g, y, eyre);
+}
+
+static double lambda_read(const ch_grid *g, int eyre) {
+    if (closed_form_bound(g->g)) return lambda_from_minmax(g->g, g->hctrl->red[4], g->hctrl->red[5], eyre);
+    return g->hctrl->red[4];
+}
+
 // Eq. (p); -1 when tau * lambda_max is not finite or p would exceed 10^6 (checked on the
 // double, before the conversion to int)
 static int cheb_order(double tau, double lmax) {
@@ -200,6 +219,13 @@ static void rhs(ch_grid *g, const double *y, double *out, int eyre, int mode,
 // columns are never combined.  Eight per launch halves the phi launches of a run to m_max
 // = 30 against four, for at most four more speculative iterations when a run stops early.
 constexpr int kPhiBlock = 8;
+
+// Krylov dimensions per projected-phi launch for this grid.  Speculative iterations cost
+// an Arnoldi iteration each (about 1 us per 1e4 points: 3-4 ms at 512^3), a phi launch tens
+// of microseconds whatever the grid, so large grids decide after every iteration and small
+// ones (launch-latency bound) batch eight.
+constexpr int64_t kPhiEveryIterPoints = (int64_t)1 << 22;
+static int phi_block(const ch_grid *g) { return g->g.N >= kPhiEveryIterPoints ? 1 : kPhiBlock; }
 
 // Kernels of Arnoldi iterations j0..j1 (Fig. 2), the projected phi and residual
 // tests of those dimensions, and the copy of the device `active` flag to pinned memory.
@@ -276,7 +302,7 @@ static ch_status krylov_run_t(ch_grid *g, const double *y0, VT *slot0, VT *V, co
     const Launch &L = g->L;
     ch::launch_krylov_arm(L, tau0, tol_phi_fixed, tol, use_ghat);
     const bool graphs = g->use_graphs && g->timing.cls < 0;
-    const int B = mmax <= 63 ? kPhiBlock : 1;
+    const int B = mmax <= 63 ? phi_block(g) : 1;
     int prev_j1 = 0;
     for (int j0 = 1; j0 <= mmax; j0 += B) {
         const int j1 = std::min(j0 + B - 1, mmax);
@@ -668,9 +694,19 @@ ch_status ch_lambda_max_bound(int dim, const int64_t n[3], double eps, int eyre,
 
 ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
                          int mmax_capacity, void *cuda_stream, ch_grid **out) {
+    return ch_create_grid_ex(dim, n, eps, precision, mmax_capacity, nullptr, cuda_stream, out);
+}
+
+ch_status ch_create_grid_ex(int dim, const int64_t n[3], double eps, int precision,
+                            int mmax_capacity, const ch_grid_options *opts, void *cuda_stream,
+                            ch_grid **out) {
     g_last_error[0] = 0;
     if (!out || !n) return fail(CH_EINVAL, "null argument");
     *out = nullptr;
+    const int bc = opts ? opts->bc : CH_BC_PERIODIC;
+    const int var_mob = opts ? opts->variable_mobility : 0;
+    if (bc != CH_BC_PERIODIC && bc != CH_BC_NEUMANN) return fail(CH_EINVAL, "unknown boundary condition");
+    if (var_mob != 0 && var_mob != 1) return fail(CH_EINVAL, "variable_mobility must be 0 or 1");
     if (dim != 2 && dim != 3) return fail(CH_EINVAL, "dim must be 2 or 3");
     int64_t N = 1;
     for (int a = 0; a < dim; ++a) {
@@ -684,6 +720,8 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
 
     ch_grid *g = new ch_grid();
     fill_geom(g->g, dim, n, eps);
+    g->g.bc = bc;
+    g->var_mobility = var_mob;
     g->precision = precision;
     g->mmax_cap = mmax_capacity;
     g->stream = (cudaStream_t)cuda_stream;
@@ -747,6 +785,13 @@ ch_status ch_create_grid(int dim, const int64_t n[3], double eps, int precision,
             e = cudaMalloc((void **)&g->gram, sizeof(double) * (size_t)(mmax_capacity + 1) * (mmax_capacity + 1));
         if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of Gram workspace", e); }
     }
+    if (var_mob) {    // face mobilities per axis (FP64, and FP32 on mixed grids)
+        for (int a = 0; a < dim; ++a) {
+            e = cudaMalloc((void **)&g->mfb[a], vb);
+            if (e == cudaSuccess && precision == CH_MIXED) e = cudaMalloc((void **)&g->mffb[a], (size_t)ld * sizeof(float));
+            if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of face mobilities", e); }
+        }
+    }
     e = cudaMalloc((void **)&g->ctrl, sizeof(Ctrl));
     if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of control block", e); }
     e = cudaMemset(g->ctrl, 0, sizeof(Ctrl));
@@ -776,6 +821,10 @@ ch_status ch_destroy_grid(ch_grid *g) {
     float *fbufs[] = {g->Vf, g->Wf[0], g->Wf[1], g->Df, g->tf};
     for (float *b : fbufs)
         if (b) cudaFree(b);
+    for (int a = 0; a < 3; ++a) {
+        if (g->mfb[a]) cudaFree(g->mfb[a]);
+        if (g->mffb[a]) cudaFree(g->mffb[a]);
+    }
     if (g->gpart) cudaFree(g->gpart);
     if (g->gram) cudaFree(g->gram);
     if (g->ctrl) cudaFree(g->ctrl);
@@ -812,12 +861,33 @@ ch_status ch_jacvec(ch_grid *g, const double *y_lin, const double *v, double *w,
     return check_launch();
 }
 
+ch_status ch_set_mobility(ch_grid *g, const double *M) {
+    if (!g) return fail(CH_EINVAL, "null grid");
+    if (!g->var_mobility) return fail(CH_EINVAL, "grid created without variable_mobility");
+    const bool was = g->g.mf[0] != nullptr;
+    if (M) {
+        double *const mf[3] = {g->mfb[0], g->mfb[1], g->mfb[2]};
+        float *const mff[3] = {g->mffb[0], g->mffb[1], g->mffb[2]};
+        ch::launch_face_mob(g->L, g->g, M, mf, mff);
+        for (int a = 0; a < 3; ++a) { g->g.mf[a] = g->mfb[a]; g->g.mff[a] = g->mffb[a]; }
+    } else {
+        for (int a = 0; a < 3; ++a) { g->g.mf[a] = nullptr; g->g.mff[a] = nullptr; }
+    }
+    // captured Arnoldi graphs hold the geometry by value: drop them when the operator form changes
+    if (was != (M != nullptr)) {
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+        for (auto &kv : g->graphs) if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        g->graphs.clear();
+    }
+    return check_launch();
+}
+
 ch_status ch_lambda_max(ch_grid *g, const double *y, int eyre, double *lambda_max) {
     if (!g || !y || !lambda_max) return fail(CH_EINVAL, "null argument");
-    ch::launch_prep(g->L, g->g, y, eyre, g->D, nullptr, 1);
+    lambda_queue(g, y, eyre);
     CH_TRY(check_launch());
     CH_TRY(sync_ctrl(g));
-    *lambda_max = lambda_from_minmax(g->g, g->hctrl->red[4], g->hctrl->red[5], eyre);
+    *lambda_max = lambda_read(g, eyre);
     return CH_OK;
 }
 
@@ -983,10 +1053,10 @@ ch_status ch_integrate(ch_grid *g, const ch_params *prm, double *y, ch_stats *st
         st.rhs_evals += 1;
     }
     if (prm->scheme == CH_LIM) {
-        ch::launch_prep(g->L, g->g, ycur, eyre, g->D, nullptr, 1);
+        lambda_queue(g, ycur, eyre);
         CH_TRY(check_launch());
         CH_TRY(sync_ctrl(g));
-        lmax = lambda_from_minmax(g->g, g->hctrl->red[4], g->hctrl->red[5], eyre);
+        lmax = lambda_read(g, eyre);
     }
     ch_status rc = CH_OK;
     for (;;) {
@@ -1029,7 +1099,7 @@ ch_status ch_integrate(ch_grid *g, const ch_params *prm, double *y, ch_stats *st
                                 0.5 * tau, 4);
                 st.rhs_evals += 1;
             }
-            ch::launch_prep(g->L, g->g, ynew, eyre, g->D, nullptr, 1);
+            lambda_queue(g, ynew, eyre);
             rc = check_launch();
             if (rc != CH_OK) break;
             rc = sync_ctrl(g);
@@ -1038,7 +1108,7 @@ ch_status ch_integrate(ch_grid *g, const ch_params *prm, double *y, ch_stats *st
                 est = sqrt(g->hctrl->red[2]) / sqrt(g->hctrl->red[3]);
                 cur = 1 - cur;
             }
-            lmax = lambda_from_minmax(g->g, g->hctrl->red[4], g->hctrl->red[5], eyre);
+            lmax = lambda_read(g, eyre);
         }
         if (adaptive && !isfinite(est)) { rc = fail(CH_ENONFINITE, "non-finite error estimate"); break; }
         r.tau = taken; r.est = est;

@@ -14,6 +14,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -253,15 +254,18 @@ kb_rhs2(const Inst *insts, const Chunk *chunks, const BState *bs, Ctrl *ctrls,
 }
 
 // ---- Krylov start of every instance still before T: clipping (Fig. 4), start vector (Fig. 2)
+// A device-driven run passes its step counter: once max_steps batch steps are taken the
+// remaining steps of the graph pass leave every instance where it is (no Krylov run, the
+// combine carries y over, the control skips the instance).
 __global__ void kb_arm(Ctrl *ctrls, BState *bs, int count, double T, double tol_phi_fixed,
-                       double tol) {
+                       double tol, const long long *steps, long long max_steps) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     Ctrl *c = ctrls + i;
     BState *b = bs + i;
     c->jexit = 0; c->converged = 0; c->shrunk = 0; c->phi_evals = 0;
     c->hnext2 = 0.0; c->resnorm = 0.0;
-    if (b->done) { c->active = 0; return; }
+    if (b->done || (steps && *steps >= max_steps)) { c->active = 0; return; }
     b->clipped = 0;
     if (b->t + b->tau > T) { b->tau = T - b->t; b->clipped = 1; }
     const double beta = sqrt(c->red[0]);
@@ -383,6 +387,231 @@ kb_mgs(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, VT *__restrict__ w,
     }
 }
 
+// ---- Gram-corrected Arnoldi iteration of FP32 batches (mixed precision, j <= kBGsMaxJ) ----
+// The coefficients of Fig. 2's modified Gram-Schmidt satisfy, for any computed basis,
+//     h_kj = c_k - sum_{i<k} G_ki h_ij,   c_k = v_k . w,   G_ki = v_k . v_i,
+// so one sweep over the basis gives every c_k and the Gram row of v_j, a forward
+// substitution per instance gives the h_kj, and a second sweep applies the update and
+// forms the new norm: three launches per iteration whatever j, instead of j + 2.
+//   kbg_stage2A: w = gam_j A (stage-1 output), c_k and G_jk partials per chunk; the last
+//                chunk of an instance sums its chunks' partials in chunk order and solves
+//                for h_kj (H, update coefficients upd_k = h_kj gam_{k-1});
+//   kbg_roundB:  w -= sum_k upd_k W_k, ||w||^2; the instance's last chunk stores h_{j+1,j}.
+// j comes from the kernel argument, or from *jp when jp is given (device-driven loop).
+constexpr int kBGsMaxJ = 31;
+constexpr int kBGsSlots = 64;         // partials per chunk: c_k in [0, 32), G_jk in [32, 64)
+
+// Block sums (256 threads) of nv <= 8 compensated per-thread pairs acc[q], written as
+// double-float pairs to out[q] (fixed order: deterministic).
+__device__ __forceinline__ void bgs_block_sums(const float2 (&acc)[8], int nv, float2 *out) {
+    __shared__ float2 red[8][kThreads];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) red[q][tid] = acc[q];
+    __syncthreads();
+    const int q1 = tid >> 5, lane = tid & 31;                 // warp q1 adds value q1
+    if (q1 < nv) {
+        const float2 *p = &red[q1][lane * 8];
+        float2 a = ch::ff_add(ch::ff_add(ch::ff_add(p[0], p[1]), ch::ff_add(p[2], p[3])),
+                              ch::ff_add(ch::ff_add(p[4], p[5]), ch::ff_add(p[6], p[7])));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float2 c;
+            c.x = __shfl_down_sync(0xffffffffu, a.x, o);
+            c.y = __shfl_down_sync(0xffffffffu, a.y, o);
+            a = ch::ff_add(a, c);
+        }
+        if (lane == 0) out[q1] = a;
+    }
+    __syncthreads();
+}
+
+// compensated running sum of FP32 values (two-sum), kept as a (sum, correction) pair
+__device__ __forceinline__ void bgs_acc(float2 &a, float p) {
+    const float t = __fadd_rn(a.x, p);
+    const float bp = __fsub_rn(t, a.x);
+    a.y = __fadd_rn(a.y, __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+    a.x = t;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+kbg_stage2A(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, const float *__restrict__ t,
+            float *__restrict__ V, int64_t ldv, const float *__restrict__ slot0, int jarg,
+            const int *jp, float2 *gpart, unsigned int *tickets, double *Hs, int64_t hstride,
+            int ldh, double *grams, int64_t gstride, int ldg) {
+    CHUNK_BEGIN
+    Ctrl *ctrl = ctrls + ck.inst;
+    if (!ctrl->active) return;
+    const int j = jp ? *jp : jarg;
+    auto W = [&](int c) -> const float * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * ldv; };
+    float *w = V + (int64_t)(j - 1) * ldv;                   // slot of W_{j+1}
+    const float gam = (float)ctrl->gam[j - 1];
+    const float c1 = gam * (float)I.s[0], c2 = gam * (float)I.s[1], c3 = gam * (float)I.s[2];
+    const float *ti = t + I.off;
+    // ---- stage 2: w = gam_j A t (difference form, FP32)
+    CHUNK_LOOP(l) {
+        float q[3];
+        pair_diffs_inst<DIM>(I, ti, l, q);
+        float r = c1 * q[0];
+        r = fmaf(c2, q[1], r);
+        if (DIM == 3) r = fmaf(c3, q[2], r);
+        w[I.off + l] = r;
+    }
+    // ---- round A: per-chunk partials of W_k . w (k <= j) and W_j . W_k (k < j), four
+    //      columns per sweep over this thread's points (its own w values: no barrier)
+    const float *xj = W(j);
+    float2 *part = gpart + (size_t)blockIdx.x * kBGsSlots;
+    __shared__ float2 bout[8];
+    for (int k0 = 1; k0 <= j; k0 += 4) {
+        const int nk = min(4, j - k0 + 1);
+        float2 acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+        CHUNK_LOOP(l) {
+            const int64_t gi = I.off + l;
+            const float wv = w[gi], xv = xj[gi];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (u < nk) {
+                    const float v = W(k0 + u)[gi];
+                    bgs_acc(acc[u], wv * v);
+                    if (k0 + u < j) bgs_acc(acc[4 + u], xv * v);
+                }
+        }
+        bgs_block_sums(acc, 8, bout);
+        if (threadIdx.x == 0)
+            for (int u = 0; u < nk; ++u) {
+                part[k0 - 1 + u] = bout[u];
+                if (k0 + u < j) part[32 + k0 - 1 + u] = bout[4 + u];
+            }
+    }
+    // ---- the instance's last chunk: sums over its chunks in order, then h_kj
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(&tickets[ck.inst], 1u) == (unsigned)I.nchunks - 1u);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ double cs[kBGsMaxJ + 1];
+    __shared__ float gs[kBGsMaxJ][kBGsMaxJ + 2];       // G_ki (k > i), 0-based
+    __shared__ double gms[kBGsMaxJ + 1];
+    double *gram = grams + ck.inst * gstride;
+    for (int e = threadIdx.x; e < j; e += blockDim.x) gms[e] = ctrl->gam[e];
+    for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
+        const int k = e / j, i = e % j;
+        gs[k][i] = (i < k && k < j - 1) ? (float)gram[(size_t)k * ldg + i] : 0.f;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < 64; v += blockDim.x) {
+        const bool isc = v < 32;
+        const int k = isc ? v : v - 32;                   // 0-based column
+        if ((isc && k < j) || (!isc && k < j - 1)) {
+            double sum = 0.0;
+            for (int c = 0; c < I.nchunks; ++c) {
+                const float2 pv = __ldcg(gpart + (size_t)(I.first_chunk + c) * kBGsSlots + v);
+                sum += (double)pv.x + (double)pv.y;
+            }
+            if (isc) {
+                cs[k] = gms[k] * sum;                                  // c_k = v_k . w
+            } else {
+                const double gji = gms[j - 1] * gms[k] * sum;          // G_jk = v_j . v_k
+                gs[j - 1][k] = (float)gji;
+                gram[(size_t)(j - 1) * ldg + k] = gji;
+            }
+        }
+    }
+    __syncthreads();
+    // forward substitution h_k = c_k - sum_{i<k} G_ki h_i (lane k-1 of warp 0): the sweeps
+    // h <- c - G h (FP32 corrections, small next to c_k) until they no longer change, else the
+    // sequential substitution; h_k itself is FP64
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        __shared__ float hsm[32];
+        const double r = l < j ? cs[l] : 0.0;
+        const float rf = (float)r;
+        float corr = 0.f;
+        bool done = false;
+        for (int sweep = 0; sweep < 4 && !done; ++sweep) {
+            hsm[l] = __fsub_rn(rf, corr);
+            __syncwarp();
+            float c2s = 0.f;
+            if (l < j)
+                for (int i = 0; i < l; ++i) c2s = __fmaf_rn(gs[l][i], hsm[i], c2s);
+            __syncwarp();
+            done = __all_sync(0xffffffffu, c2s == corr);
+            corr = c2s;
+        }
+        if (!done) {
+            corr = 0.f;
+            for (int i = 0; i < j; ++i) {
+                const float gcur = (l > i && l < j) ? gs[l][i] : 0.f;
+                const float hi = __shfl_sync(0xffffffffu, __fsub_rn(rf, corr), i);
+                corr = __fmaf_rn(gcur, hi, corr);
+            }
+        }
+        if (l < j) {
+            const double h = r - (double)corr;
+            ctrl->upd[l] = h * gms[l];
+            Hs[ck.inst * hstride + (size_t)l * ldh + (j - 1)] = h;
+        }
+    }
+    if (threadIdx.x == 0) tickets[ck.inst] = 0u;
+}
+
+__global__ void __launch_bounds__(kThreads)
+kbg_roundB(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, float *__restrict__ V, int64_t ldv,
+           const float *__restrict__ slot0, int jarg, const int *jp, float2 *gpart,
+           unsigned int *tickets, double *Hs, int64_t hstride, int ldh) {
+    CHUNK_BEGIN
+    Ctrl *ctrl = ctrls + ck.inst;
+    if (!ctrl->active) return;
+    const int j = jp ? *jp : jarg;
+    auto W = [&](int c) -> const float * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * ldv; };
+    float *w = V + (int64_t)(j - 1) * ldv;
+    __shared__ float as[kBGsMaxJ];
+    for (int e = threadIdx.x; e < j; e += blockDim.x) as[e] = (float)ctrl->upd[e];
+    __syncthreads();
+    float2 acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+    CHUNK_LOOP(l) {
+        const int64_t gi = I.off + l;
+        float x = w[gi];
+        for (int k0 = 1; k0 <= j; k0 += 8) {           // eight column loads in flight
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = k0 + u <= j ? W(k0 + u)[gi] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k0 + u <= j) x = __fmaf_rn(-as[k0 + u - 1], v[u], x);
+        }
+        w[gi] = x;
+        bgs_acc(acc[0], x * x);
+    }
+    __shared__ float2 bout[8];
+    bgs_block_sums(acc, 1, bout);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        gpart[(size_t)blockIdx.x * kBGsSlots] = bout[0];
+        __threadfence();
+        last = (atomicAdd(&tickets[ck.inst], 1u) == (unsigned)I.nchunks - 1u);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double nrm2 = 0.0;
+    for (int c = 0; c < I.nchunks; ++c) {
+        const float2 pv = __ldcg(gpart + (size_t)(I.first_chunk + c) * kBGsSlots);
+        nrm2 += (double)pv.x + (double)pv.y;
+    }
+    ctrl->hnext2 = nrm2;
+    Hs[ck.inst * hstride + (size_t)j * ldh + (j - 1)] = sqrt(nrm2);     // h_{j+1,j} (Fig. 2)
+    tickets[ck.inst] = 0u;
+}
+
 // 1 in *flag when some instance's Krylov run is still active.
 __global__ void kb_any(const Ctrl *ctrls, int count, int *flag) {
     __shared__ int any;
@@ -392,6 +621,24 @@ __global__ void kb_any(const Ctrl *ctrls, int count, int *flag) {
         if (ctrls[i].active) any = 1;
     __syncthreads();
     if (threadIdx.x == 0) *flag = any;
+}
+
+// Gate of Arnoldi iteration j in a device-driven step: the condition of that iteration's
+// conditional node is 1 while some instance's Krylov run is still active, so iterations
+// after every run has ended cost one small launch.  Kernel launches are tallied in *nlaunch
+// (this one, plus the iteration's `iter_kernels` when it runs).
+__global__ void kb_gate(const Ctrl *ctrls, int count, cudaGraphConditionalHandle h,
+                        unsigned long long *nlaunch, int iter_kernels) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < count; i += blockDim.x)
+        if (ctrls[i].active) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cudaGraphSetConditional(h, any ? 1u : 0u);
+        atomicAdd(nlaunch, 1ull + (any ? (unsigned long long)iter_kernels : 0ull));
+    }
 }
 
 // ---- Krylov combine of Fig. 2 per instance; finished instances carry y over ---------------
@@ -445,15 +692,21 @@ kb_combine32b(const Inst *insts, const Chunk *chunks, const BState *bs, const Ct
 }
 
 // ---- Fig. 4 per instance: est, time, next step size (Eq. EEdt), counters -----------------
+// With `steps` (device-driven runs) the control also counts batch steps and, when cond_set,
+// sets the condition of the graph's step loop: run on while an instance is before T and
+// fewer than max_steps batch steps were taken.
 __global__ void kb_control(Ctrl *ctrls, BState *bs, int count, double T, double tol,
-                           int *remaining) {
+                           int *remaining, long long *steps, long long max_steps, int cond_set,
+                           cudaGraphConditionalHandle cond, unsigned long long *nlaunch,
+                           int step_kernels) {
     __shared__ int rem;
     if (threadIdx.x == 0) rem = 0;
     __syncthreads();
+    const bool halted = steps && *steps >= max_steps;
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
         Ctrl *c = ctrls + i;
         BState *b = bs + i;
-        if (!b->done) {
+        if (!b->done && !halted) {
             if (c->status != 0) {
                 b->status = c->status;
                 b->done = 1;
@@ -478,7 +731,15 @@ __global__ void kb_control(Ctrl *ctrls, BState *bs, int count, double T, double 
         if (!b->done) atomicAdd(&rem, 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) *remaining = rem;
+    if (threadIdx.x == 0) {
+        *remaining = rem;
+        if (steps) {
+            const long long k = halted ? *steps : *steps + 1;
+            *steps = k;
+            *nlaunch += (unsigned long long)step_kernels;
+            if (cond_set) cudaGraphSetConditional(cond, (rem > 0 && k < max_steps) ? 1u : 0u);
+        }
+    }
 }
 
 __global__ void kb_init(BState *bs, Ctrl *ctrls, int count, double tau0) {
@@ -512,6 +773,13 @@ struct ch_batch {
     unsigned int *tickets;
     void *D, *t, *V, *W[2];  // basis precision
     int *dflags;             // [0] any active, [1] remaining
+    long long *dsteps;       // batch steps taken by a device-driven run
+    float2 *gpart;           // mixed batches: chunk partials of the Gram-corrected iteration
+    double *grams;           // mixed batches: Gram matrix of each instance's basis
+    cudaGraphExec_t run_exec;               // device-driven integration (one graph launch)
+    unsigned long long *dlaunch;            // kernels a device-driven run executed
+    cudaStream_t cap_stream2;               // second capture stream (conditional bodies)
+    std::vector<double> run_key;            // parameters the run graph was built for
     int *hflags;             // pinned: [0],[1] any active (alternating), [2] remaining
     cudaEvent_t ev[2];
     int64_t launches;
@@ -562,25 +830,47 @@ VT *basis_col(ch_batch *b, int slot, int c) {   // W_c, 1-based
     return (VT *)b->V + (int64_t)(c - 2) * b->Ntot;
 }
 
+// Kernels of Arnoldi iteration j of every active instance (Fig. 2) and the projected phi
+// with its residual test: the Gram-corrected form (three launches) on FP32 batches with
+// m_max <= kBGsMaxJ, the sequential modified Gram-Schmidt passes otherwise.  jp: the
+// device-held j of a device-driven loop (nullptr: j as given).
 template <typename VT>
-void queue_iteration_b(ch_batch *b, cudaStream_t s, int slot, int j, int mmax) {
+void queue_arnoldi_b(ch_batch *b, cudaStream_t s, int slot, int j, int mmax) {
     const int ldh = b->mmax_cap;
     const int64_t hs = (int64_t)(b->mmax_cap + 1) * b->mmax_cap;
     VT *Wj = basis_col<VT>(b, slot, j), *Wn = basis_col<VT>(b, slot, j + 1), *v1 = basis_col<VT>(b, slot, 1);
     BLAUNCH_T(kb_tstage, VT, b->insts, b->chunks, b->ctrls, Wj, (const VT *)b->D, (VT *)b->t);
-    BLAUNCH_T(kb_wstage, VT, b->insts, b->chunks, b->ctrls, (const VT *)b->t, Wn, v1, b->H, hs, ldh,
-              j, b->partials, b->nchunks, b->tickets);
-    for (int k = 1; k <= j; ++k) {
-        const int last = k == j;
-        kb_mgs<VT><<<b->nchunks, kThreads, 0, s>>>(b->insts, b->chunks, b->ctrls, Wn,
-                                                    basis_col<VT>(b, slot, k),
-                                                    last ? nullptr : basis_col<VT>(b, slot, k + 1),
-                                                    b->H, hs, ldh, j, k, last, b->partials,
-                                                    b->nchunks, b->tickets);
+    if (sizeof(VT) == 4 && b->gpart && j <= kBGsMaxJ) {
+        const int ldg = b->mmax_cap + 1;
+        const int64_t gst = (int64_t)ldg * ldg;
+        BLAUNCH(kbg_stage2A, b->insts, b->chunks, b->ctrls, (const float *)b->t, (float *)b->V, b->Ntot,
+                (const float *)v1, j, (const int *)nullptr, b->gpart, b->tickets, b->H, hs, ldh, b->grams,
+                gst, ldg);
+        kbg_roundB<<<b->nchunks, kThreads, 0, s>>>(b->insts, b->chunks, b->ctrls, (float *)b->V, b->Ntot,
+                                                   (const float *)v1, j, nullptr, b->gpart, b->tickets, b->H,
+                                                   hs, ldh);
         ++b->launches;
+    } else {
+        BLAUNCH_T(kb_wstage, VT, b->insts, b->chunks, b->ctrls, (const VT *)b->t, Wn, v1, b->H, hs, ldh,
+                  j, b->partials, b->nchunks, b->tickets);
+        for (int k = 1; k <= j; ++k) {
+            const int last = k == j;
+            kb_mgs<VT><<<b->nchunks, kThreads, 0, s>>>(b->insts, b->chunks, b->ctrls, Wn,
+                                                        basis_col<VT>(b, slot, k),
+                                                        last ? nullptr : basis_col<VT>(b, slot, k + 1),
+                                                        b->H, hs, ldh, j, k, last, b->partials,
+                                                        b->nchunks, b->tickets);
+            ++b->launches;
+        }
     }
     Launch L = make_launch(b, s);
     ch::launch_phi_batch(L, b->ctrls, b->H, hs, b->u, b->mmax_cap + 1, ldh, j, mmax, b->count);
+}
+
+// Host-driven form: iteration j, then the "any run active" flag copied to pinned memory.
+template <typename VT>
+void queue_iteration_b(ch_batch *b, cudaStream_t s, int slot, int j, int mmax) {
+    queue_arnoldi_b<VT>(b, s, slot, j, mmax);
     kb_any<<<1, 256, 0, s>>>(b->ctrls, b->count, &b->dflags[0]);
     ++b->launches;
     cudaMemcpyAsync(&b->hflags[j & 1], &b->dflags[0], sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -640,7 +930,7 @@ ch_status integrate_b(ch_batch *b, const ch_params *prm, double *y, ch_stats *st
     ch_status rc = CH_OK;
     for (;;) {
         kb_arm<<<(b->count + 255) / 256, 256, 0, s>>>(b->ctrls, b->bs, b->count, prm->T,
-                                                      prm->tol_phi, prm->tol);
+                                                      prm->tol_phi, prm->tol, nullptr, 0);
         kb_prep<VT><<<b->nchunks, kThreads, 0, s>>>(b->insts, b->chunks, b->bs, ycur, (VT *)b->D);
         ++b->launches;
         BTRY(krylov_b<VT>(b, cur, prm->mmax, use_graphs));
@@ -651,7 +941,8 @@ ch_status integrate_b(ch_batch *b, const ch_params *prm, double *y, ch_stats *st
             kb_combine32b<<<b->nchunks, kThreads, 0, s>>>(b->insts, b->chunks, b->bs, b->ctrls,
                                                            ycur, (float *)b->t, ynew);
         rhs_b<VT>(b, s, ynew, 1 - cur, 1, ycur, b->F[cur]);           // est, f(y^{n+1})
-        kb_control<<<1, 256, 0, s>>>(b->ctrls, b->bs, b->count, prm->T, prm->tol, &b->dflags[1]);
+        kb_control<<<1, 256, 0, s>>>(b->ctrls, b->bs, b->count, prm->T, prm->tol, &b->dflags[1], nullptr,
+                                     0, 0, cudaGraphConditionalHandle{}, nullptr, 0);
         BCUDA(cudaGetLastError());
         BCUDA(cudaMemcpyAsync(&b->hflags[2], &b->dflags[1], sizeof(int), cudaMemcpyDeviceToHost, s));
         BCUDA(cudaStreamSynchronize(s));
@@ -668,6 +959,151 @@ ch_status integrate_b(ch_batch *b, const ch_params *prm, double *y, ch_stats *st
     std::vector<BState> hb(b->count);
     BCUDA(cudaMemcpyAsync(hb.data(), b->bs, b->count * sizeof(BState), cudaMemcpyDeviceToHost, s));
     BCUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < b->count; ++i) {
+        if (hb[i].status && rc == CH_OK)
+            rc = bfail((ch_status)hb[i].status, "instance %d failed (status %d) at t = %g", i, hb[i].status, hb[i].t);
+        if (stats) {
+            ch_stats &st = stats[i];
+            memset(&st, 0, sizeof st);
+            st.steps = hb[i].steps; st.matvecs = hb[i].matvecs; st.rhs_evals = hb[i].rhs_evals;
+            st.krylov_iters = hb[i].krylov_iters; st.tau_shrinks = hb[i].tau_shrinks;
+            st.phi_evals = hb[i].phi_evals; st.t = hb[i].t; st.tau_next = hb[i].tau;
+            st.last_est = hb[i].est;
+        }
+    }
+    return rc;
+}
+
+// ---- device-driven integration: the whole run is one graph launch --------------------------
+// One batch step (Fig. 4 for every instance still before T) with all m_max Arnoldi iterations
+// unrolled: the kernels of iteration j return at once for instances whose Krylov run has
+// ended, so no host decision is needed inside a step.  Slot `cur` holds f(y^n) and the start
+// vector; ycur -> ynew.  kb_control counts the step and, with cond_set, sets the loop condition.
+template <typename VT>
+ch_status queue_step_dev(ch_batch *b, cudaStream_t s, const ch_params *prm, int cur, double *ycur,
+                         double *ynew, int cond_set, cudaGraphConditionalHandle cond) {
+    const int64_t l0 = b->launches;
+    kb_arm<<<(b->count + 255) / 256, 256, 0, s>>>(b->ctrls, b->bs, b->count, prm->T, prm->tol_phi, prm->tol,
+                                                  b->dsteps, prm->max_steps);
+    kb_prep<VT><<<b->nchunks, kThreads, 0, s>>>(b->insts, b->chunks, b->bs, ycur, (VT *)b->D);
+    b->launches += 2;
+    queue_arnoldi_b<VT>(b, s, cur, 1, prm->mmax);
+    int64_t fixed = b->launches - l0;
+    for (int j = 2; j <= prm->mmax; ++j) {
+        // gate kernel, then a conditional node holding iteration j (captured on a second stream)
+        cudaStreamCaptureStatus st;
+        cudaGraph_t cg = nullptr;
+        BCUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h;
+        BCUDA(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
+        const int64_t li = b->launches;
+        const int iter_kernels = (sizeof(VT) == 4 && b->gpart && j <= kBGsMaxJ) ? 4 : 3 + j;
+        kb_gate<<<1, 256, 0, s>>>(b->ctrls, b->count, h, b->dlaunch, iter_kernels);
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        BCUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd));
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        BCUDA(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np));
+        BCUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        BCUDA(cudaStreamBeginCaptureToGraph(b->cap_stream2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+        queue_arnoldi_b<VT>(b, b->cap_stream2, cur, j, prm->mmax);
+        cudaGraph_t tmp = nullptr;
+        BCUDA(cudaStreamEndCapture(b->cap_stream2, &tmp));
+        b->launches = li;                  // executed launches are tallied on the device
+    }
+    const int64_t l1 = b->launches;
+    kb_combine<VT><<<b->nchunks, kThreads, 0, s>>>(
+        b->insts, b->chunks, b->bs, b->ctrls, ycur, basis_col<VT>(b, cur, 1), (VT *)b->V, b->Ntot, ynew,
+        (float *)b->t, b->partials, b->nchunks, b->tickets);
+    ++b->launches;
+    if (sizeof(VT) == 4) {
+        kb_combine32b<<<b->nchunks, kThreads, 0, s>>>(b->insts, b->chunks, b->bs, b->ctrls, ycur,
+                                                       (float *)b->t, ynew);
+        ++b->launches;
+    }
+    rhs_b<VT>(b, s, ynew, 1 - cur, 1, ycur, b->F[cur]);                 // est, f(y^{n+1})
+    fixed += b->launches - l1 + 1;
+    kb_control<<<1, 256, 0, s>>>(b->ctrls, b->bs, b->count, prm->T, prm->tol, &b->dflags[1], b->dsteps,
+                                 prm->max_steps, cond_set, cond, b->dlaunch, (int)fixed);
+    BCUDA(cudaGetLastError());
+    return CH_OK;
+}
+
+// The run graph: a conditional while node whose body takes two batch steps, y -> ynew and
+// ynew -> y, so every pass ends with the state in the caller's y (instances that reached T
+// are carried over by the combine).  The body repeats while the second step's control finds
+// an instance before T and fewer than max_steps steps taken.  Kernel arguments (y, T, tol,
+// tau0, m_max, max_steps) are baked in: the graph is rebuilt when they change.
+template <typename VT>
+ch_status build_run_graph(ch_batch *b, const ch_params *prm, double *y) {
+    const std::vector<double> key = {(double)(uintptr_t)y, prm->T, prm->tau0, prm->tol, prm->tol_phi,
+                                     (double)prm->mmax, (double)prm->max_steps};
+    if (b->run_exec && key == b->run_key) return CH_OK;
+    if (b->run_exec) { cudaGraphExecDestroy(b->run_exec); b->run_exec = nullptr; }
+    cudaGraph_t graph = nullptr;
+    BCUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return bfail(CH_ECUDA, "conditional graph node: %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    const int64_t before = b->launches;
+    e = cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        ch_status st = queue_step_dev<VT>(b, b->cap_stream, prm, 0, y, b->ynew, 0, cond);
+        if (st == CH_OK) st = queue_step_dev<VT>(b, b->cap_stream, prm, 1, b->ynew, y, 1, cond);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(b->cap_stream, &captured);
+        if (st != CH_OK && e == cudaSuccess) e = cudaErrorStreamCaptureInvalidated;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->run_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    b->launches = before;
+    if (e != cudaSuccess) {
+        b->run_exec = nullptr;
+        cudaGetLastError();
+        return bfail(CH_ECUDA, "run graph: %s", cudaGetErrorString(e));
+    }
+    b->run_key = key;
+    return CH_OK;
+}
+
+template <typename VT>
+ch_status integrate_b_dev(ch_batch *b, const ch_params *prm, double *y, ch_stats *stats) {
+    cudaStream_t s = b->stream;
+    BTRY(build_run_graph<VT>(b, prm, y));
+    kb_init<<<(b->count + 255) / 256, 256, 0, s>>>(b->bs, b->ctrls, b->count, prm->tau0);
+    BCUDA(cudaMemsetAsync(b->dsteps, 0, sizeof(long long), s));
+    BCUDA(cudaMemsetAsync(b->dlaunch, 0, sizeof(unsigned long long), s));
+    rhs_b<VT>(b, s, y, 0, 0, nullptr, nullptr);                      // f(y^0), norms
+    BCUDA(cudaGetLastError());
+    BCUDA(cudaGraphLaunch(b->run_exec, s));
+    long long steps = 0;
+    unsigned long long ran = 0;
+    BCUDA(cudaMemcpyAsync(&b->hflags[2], &b->dflags[1], sizeof(int), cudaMemcpyDeviceToHost, s));
+    BCUDA(cudaMemcpyAsync(&steps, b->dsteps, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    BCUDA(cudaMemcpyAsync(&ran, b->dlaunch, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    std::vector<BState> hb(b->count);
+    BCUDA(cudaMemcpyAsync(hb.data(), b->bs, b->count * sizeof(BState), cudaMemcpyDeviceToHost, s));
+    BCUDA(cudaStreamSynchronize(s));
+    b->launches += 3 + (int64_t)ran;            // kb_init, f(y^0) and the graph's executed kernels
+    ch_status rc = CH_OK;
+    if (b->hflags[2] != 0) rc = bfail(CH_ENOTCONV, "max_steps reached before T");
     for (int i = 0; i < b->count; ++i) {
         if (hb[i].status && rc == CH_OK)
             rc = bfail((ch_status)hb[i].status, "instance %d failed (status %d) at t = %g", i, hb[i].status, hb[i].t);
@@ -706,14 +1142,16 @@ ch_status ch_destroy_batch(ch_batch *b) {
     cudaStreamSynchronize(b->stream);
     void *bufs[] = {b->insts, b->chunks, b->bs, b->ctrls, b->H, b->u, b->ynew, b->F[0], b->F[1],
                     b->mu, b->q, b->partials, b->tickets, b->D, b->t, b->V, b->W[0], b->W[1],
-                    b->dflags};
+                    b->dflags, b->dsteps, b->dlaunch, b->gpart, b->grams};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (b->hflags) cudaFreeHost(b->hflags);
     for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
     if (b->ev[0]) cudaEventDestroy(b->ev[0]);
     if (b->ev[1]) cudaEventDestroy(b->ev[1]);
+    if (b->run_exec) cudaGraphExecDestroy(b->run_exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->cap_stream2) cudaStreamDestroy(b->cap_stream2);
     delete b;
     return CH_OK;
 }
@@ -787,6 +1225,7 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
         {(void **)&b->tickets, sizeof(unsigned int) * count},
         {(void **)&b->D, eb}, {(void **)&b->t, std::max(eb, (size_t)off * sizeof(float))},
         {(void **)&b->V, eb * (size_t)mmax_capacity}, {(void **)&b->dflags, 2 * sizeof(int)},
+        {(void **)&b->dsteps, sizeof(long long)}, {(void **)&b->dlaunch, sizeof(unsigned long long)},
     };
     for (auto &a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -797,6 +1236,12 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
             cudaError_t e = cudaMalloc(&b->W[k], eb);
             if (e != cudaSuccess) { cudaGetLastError(); return cleanup("cudaMalloc of FP32 start vectors", e); }
         }
+        if (mmax_capacity <= kBGsMaxJ) {    // the Gram-corrected iteration's workspace
+            cudaError_t e = cudaMalloc((void **)&b->gpart, sizeof(float2) * kBGsSlots * (size_t)max_chunks);
+            if (e == cudaSuccess)
+                e = cudaMalloc((void **)&b->grams, sizeof(double) * count * (size_t)(mmax_capacity + 1) * (mmax_capacity + 1));
+            if (e != cudaSuccess) { cudaGetLastError(); return cleanup("cudaMalloc of Gram workspace", e); }
+        }
     }
     cudaError_t e = cudaMemset(b->tickets, 0, sizeof(unsigned int) * count);
     if (e == cudaSuccess) e = cudaMemset(b->ctrls, 0, sizeof(Ctrl) * count);
@@ -805,6 +1250,7 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[1], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = (cudaError_t)ch::phi_setup();
     if (e != cudaSuccess) return cleanup("batch set-up", e);
     // ---- chunk-length autotuner: time one stencil pass over the whole batch per candidate
@@ -877,6 +1323,15 @@ ch_status ch_integrate_batch(ch_batch *b, const ch_params *prm, double *y, ch_st
     if (prm->mmax < 1 || prm->mmax > b->mmax_cap) return bfail(CH_EINVAL, "mmax outside [1, capacity]");
     if (prm->max_steps < 1) return bfail(CH_EINVAL, "max_steps must be >= 1");
     ch::NvtxRange range("ch_integrate_batch EE2");
+    // The run is one graph launch (device-driven steps and Krylov iterations); CH_BATCH_HOST_LOOP=1
+    // selects the host-driven loop (one graph per Arnoldi iteration, the host reading a
+    // device flag after each), which is also taken if the run graph cannot be built.
+    const char *env = getenv("CH_BATCH_HOST_LOOP");
+    if (!(env && env[0] == '1')) {
+        const ch_status st = b->precision == CH_MIXED ? integrate_b_dev<float>(b, prm, y, stats)
+                                                      : integrate_b_dev<double>(b, prm, y, stats);
+        if (st != CH_ECUDA || b->run_exec) return st;
+    }
     return b->precision == CH_MIXED ? integrate_b<float>(b, prm, y, stats)
                                     : integrate_b<double>(b, prm, y, stats);
 }

@@ -33,8 +33,15 @@ struct NvtxRange {
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
-// Periodic grid geometry, passed by value.  -A = discrete Laplacian, h_a = 1/n_a:
-//   (A v)_i = sum_a s_a (2 v_i - v_{i+e_a} - v_{i-e_a}),   s_a = 1/h_a^2 = n_a^2.
+// Grid geometry, passed by value.  -A = discrete Laplacian, h_a = 1/n_a:
+//   (A v)_i = sum_a s_a (2 v_i - v_{i+e_a} - v_{i-e_a}),   s_a = 1/h_a^2 = n_a^2,
+// with the neighbour beyond the boundary either the periodic image (bc = 0) or, for the
+// homogeneous Neumann conditions of Eq. (CH) on cell-centred nodes (bc = 1), the mirror
+// image of the point inside, which is the point itself.  With a variable mobility (the
+// Remark on Eq. CHmob) the outer operator is the flux form
+//   (A_M t)_i = sum_a [mf_a[i] (t_i - t_{i+e_a}) + mf_a[i-e_a] (t_i - t_{i-e_a})],
+// mf_a[i] = s_a (M_i + M_{i+e_a}) / 2 the scaled mobility of the face between i and i+e_a
+// (a face to a mirror neighbour carries no flux: its difference is zero).
 struct Geom {
     int dim;
     int n[3];
@@ -42,8 +49,11 @@ struct Geom {
     int64_t st[3];      // index stride of each axis: 1, n0, n0 n1
     double s[3];        // s_a
     double kap[3];      // eps^2 s_a
-    double sigma;       // 2 sum_a s_a  (diagonal of A)
+    double sigma;       // 2 sum_a s_a  (diagonal of A away from a Neumann boundary)
     double eps2;        // eps^2
+    int bc;             // 0: periodic; 1: homogeneous Neumann, cell-centred
+    const double *mf[3];  // face mobilities (FP64); nullptr: unit mobility
+    const float *mff[3];  // FP32 copies for the mixed-precision stages (mixed grids)
 };
 
 // Device-resident control block of one grid: scalars produced by one kernel and consumed
@@ -67,7 +77,7 @@ struct Ctrl {
     double red[8];      // generic reduced scalars (norms, est sums, min/max)
     double gam[130];    // v_c = gam[c-1] W_c: scale of each stored (unnormalised) basis vector
     double coef[130];   // beta gam_c u_c: coefficients of the Krylov combine (Fig. 2)
-    double vmean[130];  // mean of each basis vector (mixed-precision mass correction)
+    double upd[130];    // batch Gram-corrected iteration: update coefficients h_kj gam_{k-1}
     double resj[130];   // resnorm(tau0) of Krylov dimension j (block-parallel phi)
     unsigned int ticket[8];
     alignas(128) unsigned long long bar;   // grid-barrier arrivals (own cache line)
@@ -136,6 +146,18 @@ __device__ __forceinline__ void grid_sum(double (&v)[K], double *partials, unsig
         fin(acc);
         *ticket = 0u;
     }
+}
+
+// Double-float (FP32 pair hi + lo) addition with a two-sum of the high parts: the sums of
+// the FP32 reductions of the mixed-precision path, in a fixed order (FP64 adds issue at a
+// small fraction of the FP32 rate on GB300).
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    const float hi = __fadd_rn(s, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
 }
 
 // Min / max variant (for lambda_max): partial pairs reduced with fmin / fmax.
@@ -263,6 +285,12 @@ void launch_resid2(const Launch &L, const Geom &g, const double *t, double *out)
 void launch_lim2(const Launch &L, const Geom &g, const double *t, const double *yn,
                  const double *yprev, double *ynext, double tau_a, double tau, double alpha);
 void launch_energy(const Launch &L, const Geom &g, const double *y);
+// Face mobilities mf_a = s_a (M_i + M_{i+e_a}) / 2 (and FP32 copies when mff[a] != nullptr)
+// from nodal values M; ||A_hat||_1 by explicit columns into red[4] (Neumann or variable-
+// mobility grids, where the periodic closed form does not hold).
+void launch_face_mob(const Launch &L, const Geom &g, const double *M, double *const mf[3],
+                     float *const mff[3]);
+void launch_colmax(const Launch &L, const Geom &g, const double *y, int eyre);
 void launch_krylov_arm(const Launch &L, double tau0, double tol_phi_fixed, double tol,
                        int use_ghat);
 

@@ -8,18 +8,24 @@
 // With D = 3 y^2 - 1 [+1 Eyre] + eps^2 sigma, kap_a = eps^2 s_a, c0 = sigma, c_a = s_a this
 // is A_hat v = A (J + eps^2 A [+ I]) v of Eqs. (A_g), (A_g_cs); other coefficient choices
 // give f(y) of Eq. (IVP), the LIM residual g_hat - A_hat y (Fig. 1) and the PC
-// estimate of Eq. (LIMest).  Neighbour indices wrap periodically.
+// estimate of Eq. (LIMest).  Neighbour indices wrap periodically, or on a Neumann grid a
+// neighbour beyond the boundary is the point itself (cell-centred mirror, Eq. CH), which
+// the same formulas then treat correctly.  With a variable mobility (the Remark on Eq.
+// CHmob) stage 2 is the flux form of A_M with the grid's face mobilities instead.
 #include <math.h>
 
 #include "ch_internal.cuh"
 
 namespace ch {
 
-__device__ __forceinline__ unsigned nb_p(unsigned i, unsigned c, unsigned n, unsigned st) {
-    return (c + 1u == n) ? i - (n - 1u) * st : i + st;
+// Neighbour of point i (coordinate c along an axis of n points and index stride st) on the
+// plus / minus side: the periodic image past the boundary (bc = 0) or the point itself
+// (bc = 1, the cell-centred Neumann mirror).
+__device__ __forceinline__ unsigned nb_p(unsigned i, unsigned c, unsigned n, unsigned st, int bc) {
+    return (c + 1u == n) ? (bc ? i : i - (n - 1u) * st) : i + st;
 }
-__device__ __forceinline__ unsigned nb_m(unsigned i, unsigned c, unsigned n, unsigned st) {
-    return (c == 0u) ? i + (n - 1u) * st : i - st;
+__device__ __forceinline__ unsigned nb_m(unsigned i, unsigned c, unsigned n, unsigned st, int bc) {
+    return (c == 0u) ? (bc ? i : i + (n - 1u) * st) : i - st;
 }
 
 // Pair sums x_{+a} + x_{-a} of the neighbours of point i along every axis.
@@ -30,12 +36,12 @@ __device__ __forceinline__ void pair_sums(const Geom &g, const T *__restrict__ x
     const unsigned c0 = i % n0;
     const unsigned r = i / n0;
     const unsigned c1 = r % n1;
-    ps[0] = x[nb_p(i, c0, n0, 1u)] + x[nb_m(i, c0, n0, 1u)];
-    ps[1] = x[nb_p(i, c1, n1, n0)] + x[nb_m(i, c1, n1, n0)];
+    ps[0] = x[nb_p(i, c0, n0, 1u, g.bc)] + x[nb_m(i, c0, n0, 1u, g.bc)];
+    ps[1] = x[nb_p(i, c1, n1, n0, g.bc)] + x[nb_m(i, c1, n1, n0, g.bc)];
     if (DIM == 3) {
         const unsigned n2 = (unsigned)g.n[2], s2 = n0 * n1;
         const unsigned c2 = r / n1;
-        ps[2] = x[nb_p(i, c2, n2, s2)] + x[nb_m(i, c2, n2, s2)];
+        ps[2] = x[nb_p(i, c2, n2, s2, g.bc)] + x[nb_m(i, c2, n2, s2, g.bc)];
     } else {
         ps[2] = T(0);
     }
@@ -50,15 +56,46 @@ __device__ __forceinline__ void pair_diffs(const Geom &g, const T *__restrict__ 
     const unsigned r = i / n0;
     const unsigned c1 = r % n1;
     const T xi = x[i];
-    pd[0] = (xi - x[nb_p(i, c0, n0, 1u)]) + (xi - x[nb_m(i, c0, n0, 1u)]);
-    pd[1] = (xi - x[nb_p(i, c1, n1, n0)]) + (xi - x[nb_m(i, c1, n1, n0)]);
+    pd[0] = (xi - x[nb_p(i, c0, n0, 1u, g.bc)]) + (xi - x[nb_m(i, c0, n0, 1u, g.bc)]);
+    pd[1] = (xi - x[nb_p(i, c1, n1, n0, g.bc)]) + (xi - x[nb_m(i, c1, n1, n0, g.bc)]);
     if (DIM == 3) {
         const unsigned n2 = (unsigned)g.n[2], s2 = n0 * n1;
         const unsigned c2 = r / n1;
-        pd[2] = (xi - x[nb_p(i, c2, n2, s2)]) + (xi - x[nb_m(i, c2, n2, s2)]);
+        pd[2] = (xi - x[nb_p(i, c2, n2, s2, g.bc)]) + (xi - x[nb_m(i, c2, n2, s2, g.bc)]);
     } else {
         pd[2] = T(0);
     }
+}
+
+// Face mobilities of axis a in precision T (FP64 or the FP32 copies of a mixed grid).
+template <typename T> __device__ __forceinline__ const T *face_mob(const Geom &g, int a);
+template <> __device__ __forceinline__ const double *face_mob<double>(const Geom &g, int a) { return g.mf[a]; }
+template <> __device__ __forceinline__ const float *face_mob<float>(const Geom &g, int a) { return g.mff[a]; }
+
+// Flux form of the outer operator with variable mobility (the Remark on Eq. CHmob) at i:
+//   (A_M t)_i = sum_a [mf_a[i] (t_i - t_{i+e_a}) + mf_a[i-e_a] (t_i - t_{i-e_a})],
+// the face on the minus side being the plus face of the minus neighbour (a Neumann mirror
+// neighbour is the point itself, so that face's difference is zero).
+template <int DIM, typename T>
+__device__ __forceinline__ T flux_at(const Geom &g, const T *__restrict__ t, unsigned i) {
+    const unsigned n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    const unsigned c0 = i % n0, r = i / n0, c1 = r % n1;
+    const T ti = t[i];
+    const T *m0 = face_mob<T>(g, 0), *m1 = face_mob<T>(g, 1);
+    unsigned p = nb_p(i, c0, n0, 1u, g.bc), m = nb_m(i, c0, n0, 1u, g.bc);
+    T acc = m0[i] * (ti - t[p]);
+    acc = fma(m0[m], ti - t[m], acc);
+    p = nb_p(i, c1, n1, n0, g.bc); m = nb_m(i, c1, n1, n0, g.bc);
+    acc = fma(m1[i], ti - t[p], acc);
+    acc = fma(m1[m], ti - t[m], acc);
+    if (DIM == 3) {
+        const unsigned n2 = (unsigned)g.n[2], s2 = n0 * n1, c2 = r / n1;
+        const T *m2 = face_mob<T>(g, 2);
+        p = nb_p(i, c2, n2, s2, g.bc); m = nb_m(i, c2, n2, s2, g.bc);
+        acc = fma(m2[i], ti - t[p], acc);
+        acc = fma(m2[m], ti - t[m], acc);
+    }
+    return acc;
 }
 
 // The two stages of A_hat v in the basis precision, at point i.
@@ -86,9 +123,12 @@ __device__ __forceinline__ VT stage1_at(const Geom &g, const VT *__restrict__ x,
     if (DIM == 3) acc = fma(k2, q[2], acc);
     return acc;
 }
+// gm: the scale the coefficients carry (gam_j, or 1); with a variable mobility stage 2 is
+// gm (A_M t)_i by the flux form instead.
 template <int DIM, typename VT>
 __device__ __forceinline__ VT stage2_at(const Geom &g, const VT *__restrict__ t, unsigned i,
-                                        VT c0, VT c1, VT c2, VT c3) {
+                                        VT c0, VT c1, VT c2, VT c3, VT gm) {
+    if (g.mf[0]) return gm * flux_at<DIM, VT>(g, t, i);
     VT q[3];
     VT r;
     if constexpr (sizeof(VT) == 8) {
@@ -223,7 +263,7 @@ k_wstage(Geom g, const VT *__restrict__ t, VT *__restrict__ w, const VT *__restr
              c3 = (VT)(gam * g.s[2]);
     DotAcc<VT> acc;
     GRID_LOOP2(g.N, {
-        const VT r = stage2_at<DIM, VT>(g, t, i, c0, c1, c2, c3);
+        const VT r = stage2_at<DIM, VT>(g, t, i, c0, c1, c2, c3, (VT)gam);
         w[i] = r;
         if (v1) acc.add(r, v1[i]);
     })
@@ -462,7 +502,7 @@ k_arnoldi(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv, const
                  c3 = (VT)(gam * g.s[2]);
         DotAcc<VT> acc;
         GRID_LOOP2(N, {
-            const VT r = stage2_at<DIM, VT>(g, t, i, c0, c1, c2, c3);
+            const VT r = stage2_at<DIM, VT>(g, t, i, c0, c1, c2, c3, (VT)gam);
             w[i] = r;
             acc.add(r, v1[i]);
         })
@@ -559,7 +599,7 @@ k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
         DotAcc<VT> acc;
         int slot = me;
         GRID_LOOP2(N, {
-            const VT q = stage2_at<DIM, VT>(g, t, i, c0, c1, c2, c3);
+            const VT q = stage2_at<DIM, VT>(g, t, i, c0, c1, c2, c3, (VT)gam);
             bufW[slot] = q;
             acc.add(q, bufA[slot]);
             slot += kArnThreads;                // elements of this thread come in order
@@ -632,15 +672,6 @@ k_arnoldi_res(Geom g, VT *__restrict__ slot0, VT *__restrict__ V, int64_t ldv,
 constexpr int kGsChunk = 8;                          // values per block reduction
 constexpr int kGsSmemBytes = kGsChunk * kArnThreads * (int)sizeof(float2)      // block sums
                              + 4 * kArnThreads * (int)sizeof(float4);             // w, v_j cache
-
-__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
-    const float s = __fadd_rn(a.x, b.x);
-    const float bb = __fsub_rn(s, a.x);
-    float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
-    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
-    const float hi = __fadd_rn(s, e);
-    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
-}
 
 // Block sums of nk <= kGsChunk per-thread pairs acc[q] (1024 threads), written as pairs
 // to out[q] by the warps q.  red holds kGsChunk x 1024 pairs.
@@ -773,7 +804,8 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
     // Rows of a multiple of four points take whole groups in the stencil stages too.
     const unsigned NG = (N + 3u) / 4u, S = G * kArnThreads;
     const unsigned q0 = blockIdx.x * kArnThreads + threadIdx.x;
-    const bool rows4 = (g.n[0] & 3) == 0;
+    // (grouped stencils assume periodic rows and unit mobility; other grids take the scalar path)
+    const bool rows4 = (g.n[0] & 3) == 0 && g.bc == 0 && g.mf[0] == nullptr;
     const bool res = NG <= 2u * S;
     // ---- stage 1: t = J x + sum_a kap_a ((x - x_{+a}) + (x - x_{-a}))
     {
@@ -840,7 +872,7 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
                 float r[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (unsigned e = 0; e < 4u; ++e)
-                    if (4u * q + e < N) r[e] = stage2_at<DIM, float>(g, t, 4u * q + e, c0, c1, c2, c3);
+                    if (4u * q + e < N) r[e] = stage2_at<DIM, float>(g, t, 4u * q + e, c0, c1, c2, c3, (float)gam);
                 if (res) {
                     wsm[ri * kArnThreads + threadIdx.x] = make_float4(r[0], r[1], r[2], r[3]);
                     xsm[ri * kArnThreads + threadIdx.x] = ld4(W(j), q, 4u * q + 3u < N);
@@ -1203,22 +1235,33 @@ k_rhs2(Geom g, const double *__restrict__ mu, const double *__restrict__ q,
        unsigned int *ticket, Ctrl *ctrl) {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     if (mode & 8) half_tau = 0.5 * ctrl->tau;
+    const bool mob = g.mf[0] != nullptr;
     GRID_LOOP2(g.N, {
-        double ps[3];
-        pair_sums<DIM>(g, mu, i, ps);
-        double r = -g.sigma * mu[i];
-        r = fma(g.s[0], ps[0], r);
-        r = fma(g.s[1], ps[1], r);
-        if (DIM == 3) r = fma(g.s[2], ps[2], r);
+        double r;
+        if (mob) {
+            r = -flux_at<DIM, double>(g, mu, i);
+        } else {
+            double ps[3];
+            pair_sums<DIM>(g, mu, i, ps);
+            r = -g.sigma * mu[i];
+            r = fma(g.s[0], ps[0], r);
+            r = fma(g.s[1], ps[1], r);
+            if (DIM == 3) r = fma(g.s[2], ps[2], r);
+        }
         f[i] = r;
         if (mode & 1) acc[0] = fma(r, r, acc[0]);
         if (mode & 2) {
-            double qs[3];
-            pair_sums<DIM>(g, q, i, qs);
-            double gh = g.sigma * q[i];
-            gh = fma(-g.s[0], qs[0], gh);
-            gh = fma(-g.s[1], qs[1], gh);
-            if (DIM == 3) gh = fma(-g.s[2], qs[2], gh);
+            double gh;
+            if (mob) {
+                gh = flux_at<DIM, double>(g, q, i);
+            } else {
+                double qs[3];
+                pair_sums<DIM>(g, q, i, qs);
+                gh = g.sigma * q[i];
+                gh = fma(-g.s[0], qs[0], gh);
+                gh = fma(-g.s[1], qs[1], gh);
+                if (DIM == 3) gh = fma(-g.s[2], qs[2], gh);
+            }
             acc[1] = fma(gh, gh, acc[1]);
         }
         if (mode & 4) {
@@ -1265,13 +1308,19 @@ __global__ void __launch_bounds__(kThreads)
 k_resid2(Geom g, const double *__restrict__ t, double *__restrict__ out, double *partials,
          unsigned int *ticket, Ctrl *ctrl) {
     double acc[1] = {0.0};
+    const bool mob = g.mf[0] != nullptr;
     GRID_LOOP2(g.N, {
-        double ps[3];
-        pair_sums<DIM>(g, t, i, ps);
-        double r = g.sigma * t[i];
-        r = fma(-g.s[0], ps[0], r);
-        r = fma(-g.s[1], ps[1], r);
-        if (DIM == 3) r = fma(-g.s[2], ps[2], r);
+        double r;
+        if (mob) {
+            r = flux_at<DIM, double>(g, t, i);
+        } else {
+            double ps[3];
+            pair_sums<DIM>(g, t, i, ps);
+            r = g.sigma * t[i];
+            r = fma(-g.s[0], ps[0], r);
+            r = fma(-g.s[1], ps[1], r);
+            if (DIM == 3) r = fma(-g.s[2], ps[2], r);
+        }
         out[i] = r;
         acc[0] = fma(r, r, acc[0]);
     })
@@ -1288,13 +1337,19 @@ k_lim2(Geom g, const double *__restrict__ t, const double *__restrict__ yn,
     const double at = alpha * tau;
     const double c0 = at * g.sigma, c1 = at * g.s[0], c2 = at * g.s[1], c3 = at * g.s[2];
     const double ca = alpha * tau_a;
+    const bool mob = g.mf[0] != nullptr;
     GRID_LOOP2(g.N, {
-        double ps[3];
-        pair_sums<DIM>(g, t, i, ps);
-        double r = c0 * t[i];
-        r = fma(-c1, ps[0], r);
-        r = fma(-c2, ps[1], r);
-        if (DIM == 3) r = fma(-c3, ps[2], r);
+        double r;
+        if (mob) {
+            r = at * flux_at<DIM, double>(g, t, i);
+        } else {
+            double ps[3];
+            pair_sums<DIM>(g, t, i, ps);
+            r = c0 * t[i];
+            r = fma(-c1, ps[0], r);
+            r = fma(-c2, ps[1], r);
+            if (DIM == 3) r = fma(-c3, ps[2], r);
+        }
         ynext[i] = fma(ca, yprev[i], fma(alpha, yn[i], r));
     })
 }
@@ -1312,12 +1367,12 @@ k_energy(Geom g, const double *__restrict__ y, double *partials, unsigned int *t
         const double u = 1.0 - yi * yi;
         double e = 0.25 * u * u;
         const unsigned c0 = i % n0, r = i / n0, c1 = r % n1;
-        double d0 = (y[nb_p(i, c0, n0, 1u)] - yi) * (double)g.n[0];
-        double d1 = (y[nb_p(i, c1, n1, n0)] - yi) * (double)g.n[1];
+        double d0 = (y[nb_p(i, c0, n0, 1u, g.bc)] - yi) * (double)g.n[0];
+        double d1 = (y[nb_p(i, c1, n1, n0, g.bc)] - yi) * (double)g.n[1];
         double gs = d0 * d0 + d1 * d1;
         if (DIM == 3) {
             const unsigned c2 = r / n1;
-            double d2 = (y[nb_p(i, c2, (unsigned)g.n[2], n0 * n1)] - yi) * (double)g.n[2];
+            double d2 = (y[nb_p(i, c2, (unsigned)g.n[2], n0 * n1, g.bc)] - yi) * (double)g.n[2];
             gs += d2 * d2;
         }
         acc[0] += fma(0.5 * g.eps2, gs, e);
@@ -1327,6 +1382,112 @@ k_energy(Geom g, const double *__restrict__ y, double *partials, unsigned int *t
         ctrl->red[6] = tot[0];
         ctrl->red[7] = tot[1];
     });
+}
+
+// ---------------------------------------------------------------------------------------
+// Face mobilities of a variable-mobility grid from nodal values M (the Remark on Eq.
+// CHmob): mf_a[i] = s_a (M_i + M_{i+e_a}) / 2, with FP32 copies when mff is given.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_face_mob(Geom g, const double *__restrict__ M, double *mf0, double *mf1, double *mf2,
+           float *mff0, float *mff1, float *mff2) {
+    const unsigned n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1], n2 = (unsigned)g.n[2];
+    double *mf[3] = {mf0, mf1, mf2};
+    float *mff[3] = {mff0, mff1, mff2};
+    GRID_LOOP(i, g.N) {
+        const unsigned c0 = i % n0, r = i / n0, c1 = r % n1, c2 = r / n1;
+        const unsigned nb[3] = {nb_p(i, c0, n0, 1u, g.bc), nb_p(i, c1, n1, n0, g.bc),
+                                nb_p(i, c2, n2, n0 * n1, g.bc)};
+        for (int a = 0; a < g.dim; ++a) {
+            const double v = g.s[a] * (0.5 * (M[i] + M[nb[a]]));
+            mf[a][i] = v;
+            if (mff[a]) mff[a][i] = (float)v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Spectral bound of Fig. 1 by explicit columns, for grids where the closed form of the
+// periodic constant-mobility operator does not hold (Neumann boundaries, variable
+// mobility): column j of A_hat is A_M (d_j e_j + eps^2 A e_j), d_j = 3 y_j^2 - 1 (+1
+// Eyre), formed entry by entry (entries falling on one point are added), and its absolute
+// sum taken; the maximum over all columns goes to red[4].
+// ---------------------------------------------------------------------------------------
+constexpr int kColMax = 32;     // distinct entries of a column: at most 25 (3D), 13 (2D)
+
+__device__ __forceinline__ int col_add(unsigned (&idx)[kColMax], double (&val)[kColMax], int cnt,
+                                       unsigned k, double v) {
+    for (int e = 0; e < cnt; ++e)
+        if (idx[e] == k) { val[e] += v; return cnt; }
+    idx[cnt] = k; val[cnt] = v;
+    return cnt + 1;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_colmax(Geom g, const double *__restrict__ y, double dshift, double *partials,
+         unsigned int *ticket, Ctrl *ctrl) {
+    const unsigned n[3] = {(unsigned)g.n[0], (unsigned)g.n[1], (unsigned)g.n[2]};
+    const unsigned st[3] = {1u, n[0], n[0] * n[1]};
+    double mn = INFINITY, mx = -INFINITY;
+    GRID_LOOP(j, g.N) {
+        // t = d_j e_j + eps^2 A e_j
+        unsigned ti[1 + 2 * 3];
+        double tv[1 + 2 * 3];
+        int nt = 1;
+        ti[0] = j; tv[0] = fma(3.0, y[j] * y[j], dshift);
+        for (int a = 0; a < g.dim; ++a) {
+            const unsigned c = (j / st[a]) % n[a];
+            const unsigned pj = nb_p(j, c, n[a], st[a], g.bc), mj = nb_m(j, c, n[a], st[a], g.bc);
+            const double k = g.eps2 * g.s[a];
+            // 2 s_a e_j - s_a e_{j+a} - s_a e_{j-a}, a mirror neighbour being j itself
+            tv[0] += 2.0 * k;
+            const unsigned nbs[2] = {pj, mj};
+            for (int q = 0; q < 2; ++q) {
+                int e = 0;
+                while (e < nt && ti[e] != nbs[q]) ++e;
+                if (e == nt) { ti[nt] = nbs[q]; tv[nt] = 0.0; ++nt; }
+                tv[e] -= k;
+            }
+        }
+        // column = A_M t: every entry k of t spreads over its faces, face by face
+        unsigned idx[kColMax];
+        double val[kColMax];
+        int cnt = 0;
+        for (int e = 0; e < nt; ++e) {
+            const unsigned k = ti[e];
+            const double v = tv[e];
+            for (int a = 0; a < g.dim; ++a) {
+                const unsigned c = (k / st[a]) % n[a];
+                const unsigned pk = nb_p(k, c, n[a], st[a], g.bc), mk = nb_m(k, c, n[a], st[a], g.bc);
+                const double fp = g.mf[a] ? g.mf[a][k] : g.s[a];     // face k | k + e_a
+                const double fm = g.mf[a] ? g.mf[a][mk] : g.s[a];    // face k - e_a | k
+                cnt = col_add(idx, val, cnt, k, fp * v);
+                cnt = col_add(idx, val, cnt, pk, -fp * v);
+                cnt = col_add(idx, val, cnt, k, fm * v);
+                cnt = col_add(idx, val, cnt, mk, -fm * v);
+            }
+        }
+        double sum = 0.0;
+        for (int e = 0; e < cnt; ++e) sum += fabs(val[e]);
+        mx = fmax(mx, sum);
+    }
+    block_minmax(mn, mx);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[gridDim.x + blockIdx.x] = mx;
+        __threadfence();
+        last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    mx = -INFINITY;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) mx = fmax(mx, __ldcg(&partials[gridDim.x + b]));
+    block_minmax(mn, mx);
+    if (threadIdx.x == 0) {
+        ctrl->red[4] = mx;
+        *ticket = 0u;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1489,6 +1650,18 @@ void launch_lim2(const Launch &L, const Geom &g, const double *t, const double *
 
 void launch_energy(const Launch &L, const Geom &g, const double *y) {
     DISPATCH_DIM(CH_K_ENERGY, g, k_energy, g, y, L.partials, &L.ctrl->ticket[0], L.ctrl);
+}
+
+void launch_face_mob(const Launch &L, const Geom &g, const double *M, double *const mf[3],
+                     float *const mff[3]) {
+    LaunchScope scope(L, CH_K_PREP);
+    k_face_mob<<<L.blocks, kThreads, 0, L.stream>>>(g, M, mf[0], mf[1], mf[2], mff[0], mff[1], mff[2]);
+}
+
+void launch_colmax(const Launch &L, const Geom &g, const double *y, int eyre) {
+    LaunchScope scope(L, CH_K_PREP);
+    k_colmax<<<L.blocks, kThreads, 0, L.stream>>>(g, y, -1.0 + (eyre ? 1.0 : 0.0), L.partials,
+                                                   &L.ctrl->ticket[0], L.ctrl);
 }
 
 void launch_krylov_arm(const Launch &L, double tau0, double tol_phi_fixed, double tol,

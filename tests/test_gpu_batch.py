@@ -106,3 +106,59 @@ def test_batch_arguments_are_validated(ch):
         assert all(s["t"] == 2e-6 for s in st)
     finally:
         ch.ch_destroy_batch(h)
+
+
+def _run_with_loop(ch, monkeypatch, host_loop, sizes, eps, y0s, precision, T, max_steps=10 ** 9):
+    monkeypatch.setenv("CH_BATCH_HOST_LOOP", "1" if host_loop else "0")
+    h = ch.ch_create_batch(2, sizes, eps, precision, 30)
+    try:
+        offs, _ = ch.ch_batch_layout(h, len(sizes))
+        y = torch.zeros(offs[-1], dtype=torch.float64, device="cuda")
+        for i, y0 in enumerate(y0s):
+            y[offs[i]:offs[i] + y0.size] = torch.from_numpy(y0).cuda()
+        l0 = ch.ch_batch_kernel_launches(h)
+        status = ch.CH_OK
+        try:
+            st = ch.ch_integrate_batch(h, ch.make_params("ee2", True, T, 1e-7, 1e-5, 30, max_steps=max_steps),
+                                       y, len(sizes))
+        except ch.CHError as e:
+            status, st = e.status, None
+        torch.cuda.synchronize()
+        yh = y.cpu().numpy()
+        return [yh[offs[i]:offs[i] + y0s[i].size] for i in range(len(sizes))], st, status, \
+            ch.ch_batch_kernel_launches(h) - l0
+    finally:
+        ch.ch_destroy_batch(h)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_device_driven_run_equals_host_driven_loop(ch, monkeypatch, precision):
+    """The whole run as one graph launch (conditional while over steps, conditional nodes
+    over Arnoldi iterations) gives bit for bit the same states and counters as the loop in
+    which the host reads a device flag after every iteration."""
+    sides = [24, 40, 64, 32]
+    eps = [0.02, 0.04, 0.03, 0.05]
+    y0s = [inputs.initial_state((s, s), 50 + i) for i, s in enumerate(sides)]
+    prec = ch.CH_FP64 if precision == "fp64" else ch.CH_MIXED
+    yd, sd, rcd, ld = _run_with_loop(ch, monkeypatch, False, sides, eps, y0s, prec, 2e-5)
+    yh, sh, rch, lh = _run_with_loop(ch, monkeypatch, True, sides, eps, y0s, prec, 2e-5)
+    assert rcd == rch == ch.CH_OK
+    for i in range(len(sides)):
+        assert np.array_equal(yd[i], yh[i]), i
+        for k in ("steps", "matvecs", "krylov_iters", "tau_shrinks", "t", "tau_next"):
+            assert sd[i][k] == sh[i][k], (i, k)
+    assert ld > 0 and lh > 0
+
+
+def test_device_driven_run_stops_at_max_steps(ch, monkeypatch):
+    """max_steps batch steps are taken exactly (also an odd number: the graph's loop body
+    holds two steps), the run reports CH_ENOTCONV and y holds the state reached, equal to
+    the host-driven loop's."""
+    sides = [32, 48]
+    eps = [0.02, 0.03]
+    y0s = [inputs.initial_state((s, s), 60 + i) for i, s in enumerate(sides)]
+    yd, _, rcd, _ = _run_with_loop(ch, monkeypatch, False, sides, eps, y0s, ch.CH_MIXED, 1e-3, max_steps=7)
+    yh, _, rch, _ = _run_with_loop(ch, monkeypatch, True, sides, eps, y0s, ch.CH_MIXED, 1e-3, max_steps=7)
+    assert rcd == rch == ch.CH_ENOTCONV
+    for a, b in zip(yd, yh):
+        assert np.array_equal(a, b)

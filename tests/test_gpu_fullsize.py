@@ -9,7 +9,9 @@ benchmark uses (one grid object per instance, m_max = 30):
 * 3D periodic 512^3 (134M points): operators against the oracle, lambda_max against the
   oracle's explicit columns where the maximum is taken; EE2 (too slow for the single-threaded
   oracle at this size) through properties that hold at any size: mass conservation and FP64
-  against mixed precision.
+  against mixed precision on a step of the same length.
+* 2D 1024^2: whole adaptive EE2 and LIM runs of tens of steps against the oracle's runs.
+* 3D 256^3: the first adaptive EE2 steps, FP64 element by element, mixed within 1e-5.
 """
 import numpy as np
 import pytest
@@ -190,6 +192,84 @@ def test_c4_first_ee2_steps_mass_and_mixed(ch, c4):
     assert abs(float(y64.mean()) - m0) < 1e-13
     assert abs(float(y32.mean()) - m0) < 1e-13
     assert 0.0 < t64 <= wl["tau0"] and 0.0 < t32 <= wl["tau0"]
-    if t32 == t64:   # same step length: the increments agree to the mixed-precision bound
-        inc = float(torch.linalg.norm(y64 - yd))
-        assert float(torch.linalg.norm(y32 - y64)) / inc < 1e-3
+
+
+def test_c4_krylov_step_fp64_against_mixed_same_length(ch, c4):
+    """One Krylov step of the same length in both precisions (linear restarting covers the
+    whole step, so neither run can cut it): the FP32-basis increment agrees with the FP64 one
+    to the mixed-precision bound u32 * max(tau lambda_max, 1), and both keep the mass."""
+    wl, n, y = c4
+    yd = dev(y)
+    tau, tphi = wl["tau0"], 1e-7
+    res = {}
+    for name, prec in (("fp64", ch.CH_FP64), ("mixed", ch.CH_MIXED)):
+        with ch.Grid(3, n, wl["eps"], prec, wl["mmax"]) as G:
+            yn = torch.empty_like(yd)
+            tu, st = ch.ch_phi_krylov(G.h, yd, tau, tphi, wl["mmax"], 1, yn)
+            assert tu == tau
+            if name == "fp64":
+                lmax = ch.ch_lambda_max(G.h, yd)
+            res[name] = yn
+    inc = float(torch.linalg.norm(res["fp64"] - yd))
+    assert inc > 0.0
+    assert float(torch.linalg.norm(res["mixed"] - res["fp64"])) / inc < 50 * U32 * max(tau * lmax, 1.0)
+    m0 = float(yd.mean())
+    for name in res:
+        assert abs(float(res[name].mean()) - m0) < 1e-13
+
+
+# ---- 2D 1024^2 and 3D 256^3: adaptive runs capped at a number of steps ---------------------
+def _capped_run(ch, dim, n, eps, prec, y0, wl, steps, cap=1000):
+    """ch_integrate with max_steps = steps through the raw C ABI (the run ends with
+    CH_ENOTCONV and the state and records of the steps taken)."""
+    import ctypes as C
+    L = ch.load()
+    with ch.Grid(dim, n, eps, prec, wl["mmax"]) as G:
+        ch.ch_set_record_capacity(G.h, cap)
+        yd = dev(y0)
+        prm = ch.make_params(wl["scheme"], True, wl["T"], wl["tau0"], wl["tol"], wl["mmax"], max_steps=steps)
+        st = ch.ch_stats()
+        rc = L.ch_integrate(G.h, C.byref(prm), C.c_void_p(yd.data_ptr()), C.byref(st))
+        assert rc in (ch.CH_OK, ch.CH_ENOTCONV), L.ch_last_error()
+        return st.as_dict(), ch.ch_get_records(G.h, cap), host(yd)
+
+
+@pytest.mark.parametrize("scheme,steps", [("ee2", 40), ("lim", 40)])
+def test_c1_adaptive_steps_against_the_oracle(ch, oracle, scheme, steps):
+    """The 1024^2 workload (tol 1e-6, tau0 1e-7) for its first 40 adaptive steps of Fig. 4 /
+    Fig. 3 (the oracle forms every column of A_hat for each LIM step, 1.6 s per step at this
+    size; the whole run to T has thousands of steps): identical step records and the state
+    within 1e-10."""
+    wl = dict(inputs.WORKLOADS["c1_2d1024_adaptive"], scheme=scheme)
+    n = (wl["n"], wl["n"])
+    y0 = inputs.initial_state(n, 0, wl["lo"], wl["hi"])
+    st, rec, yg = _capped_run(ch, 2, n, wl["eps"], ch.CH_FP64, y0, wl, steps)
+    rc, yo, to, sto, reco = oracle.integrate(oracle.Grid(2, n, wl["eps"]), y0, scheme, True, wl["T"], wl["tau0"],
+                                             tol=wl["tol"], mmax=wl["mmax"], max_steps=steps, max_rec=1000)
+    assert st["steps"] == sto["steps"] == steps
+    assert st["matvecs"] == sto["matvecs"]
+    assert st["t"] == pytest.approx(to, rel=1e-9)
+    np.testing.assert_array_equal(rec["jexit"], reco["jexit"])
+    np.testing.assert_array_equal(rec["shrunk"], reco["shrunk"])
+    np.testing.assert_array_equal(rec["p"], reco["p"])
+    np.testing.assert_allclose(rec["tau"], reco["tau"], rtol=1e-9)
+    assert rel(yg, yo) < 1e-10
+
+
+def test_c2_first_adaptive_steps(ch, oracle, c2):
+    """The 256^3 workload's first four adaptive EE2 steps: FP64 element by element, the mixed
+    run (FP32 basis and stencils) within 1e-5 of the oracle."""
+    wl, n, y = c2
+    wl = dict(wl, scheme="ee2")
+    steps = 4
+    st, rec, yg = _capped_run(ch, 3, n, wl["eps"], ch.CH_FP64, y, wl, steps)
+    rc, yo, to, sto, reco = oracle.integrate(oracle.Grid(3, n, wl["eps"]), y, "ee2", True, wl["T"], wl["tau0"],
+                                             tol=wl["tol"], mmax=wl["mmax"], max_steps=steps, max_rec=100)
+    assert st["steps"] == sto["steps"] == steps and st["matvecs"] == sto["matvecs"]
+    np.testing.assert_array_equal(rec["jexit"], reco["jexit"])
+    assert rel(yg, yo) < 1e-10
+    # the mixed run, adaptive with its own step sequence, to the time the FP64 run reached
+    stm, recm, ym = _capped_run(ch, 3, n, wl["eps"], ch.CH_MIXED, y, dict(wl, T=st["t"]), 10 ** 6)
+    assert stm["t"] == st["t"]
+    assert rel(ym, yo) < 1e-5
+    assert abs(ym.mean() - y.mean()) < 1e-13

@@ -418,3 +418,55 @@ def test_arnoldi_kernel_forms_at_size(ch, oracle, dim, n, tau):
     assert tu == pytest.approx(to, rel=1e-12, abs=0)
     assert st["matvecs"] == sto["matvecs"]
     assert rel(host(yn), yo) < 1e-12
+
+
+@pytest.mark.parametrize("dim,n,tau,mmax,lin", [(2, (64, 64), 1e-5, 30, 0), (3, (12, 12, 12), 3e-5, 30, 0),
+                                                (2, (48, 40), 4e-5, 6, 1), (2, (64, 64), 2e-4, 30, 0)])
+def test_phi_krylov_eyre(ch, oracle, dim, n, tau, mmax, lin):
+    """Eq. (A_g_cs): the Krylov run of Fig. 2 on the Eyre-split A_hat, g_hat (Sec. 4.3),
+    with the step choice of Eq. (phi_stop) or linear restarting."""
+    eps, tol_phi = 0.05, 1e-8
+    y = inputs.initial_state(n, 11, -0.4, 0.4)
+    with ch.Grid(dim, n, eps) as G:
+        yn = torch.empty(G.N, dtype=torch.float64, device="cuda")
+        tu, st = ch.ch_phi_krylov(G.h, dev(y), tau, tol_phi, mmax, lin, yn, eyre=1)
+    rc, yo, to, jo, sto = oracle.ee_step(oracle.Grid(dim, n, eps, eyre=True), y, tau, tol_phi_fixed=tol_phi,
+                                         mmax=mmax, linear_restart=bool(lin))
+    assert rc == 0
+    assert tu == pytest.approx(to, rel=1e-12, abs=0)
+    assert st["matvecs"] == sto["matvecs"] and st["restarts"] == sto["restarts"]
+    assert rel(host(yn), yo) < 1e-12
+
+
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_eyre_ee2_integration(ch, oracle, adaptive):
+    """EE2 with the Eyre splitting (Sec. 4.3, the EE2 column of Table 2), constant steps with
+    linear restarting and adaptive steps by Fig. 4: identical step sequence and solution."""
+    n, eps = (48, 48), 0.03
+    y0 = inputs.initial_state(n, 12, -0.05, 0.05)
+    if adaptive:
+        args = dict(T=2e-4, tau0=1e-7, tol=1e-5)
+    else:
+        args = dict(T=4e-5, tau0=4e-6, tol=1e-5, tol_phi=1e-8)
+    yg, st, rec, yo, sto, reco = _run_both(ch, oracle, 2, n, eps, y0, "ee2", adaptive, args["T"], args["tau0"],
+                                           tol=args["tol"], tol_phi=args.get("tol_phi", -1.0), eyre=True)
+    assert st["steps"] == sto["steps"] and st["matvecs"] == sto["matvecs"]
+    np.testing.assert_array_equal(rec["jexit"], reco["jexit"])
+    np.testing.assert_array_equal(rec["restarts"], reco["restarts"])
+    np.testing.assert_array_equal(rec["shrunk"], reco["shrunk"])
+    assert rel(yg, yo) < 1e-10
+
+
+def test_ee2_mmax100_constant_steps_with_restarts(ch, oracle):
+    """The EE2(m_max = 100) configuration of Table 1 on a periodic grid: constant steps,
+    linear residual-time restarting once a run reaches m_max, identical restarts and
+    solution (projected phi beyond 64 dimensions works from global memory)."""
+    n, eps = (40, 52), 0.05
+    y0 = inputs.initial_state(n, 6, -0.05, 0.05)
+    yg, st, rec, yo, sto, reco = _run_both(ch, oracle, 2, n, eps, y0, "ee2", False, 1.2e-3, 4e-4, mmax=100,
+                                           tol_phi=1e-8)
+    assert st["steps"] == sto["steps"] == 3
+    assert st["matvecs"] == sto["matvecs"] and max(rec["jexit"]) > 64
+    np.testing.assert_array_equal(rec["jexit"], reco["jexit"])
+    np.testing.assert_array_equal(rec["restarts"], reco["restarts"])
+    assert rel(yg, yo) < 1e-10
