@@ -1,13 +1,18 @@
 """Benchmark of the Cahn-Hilliard hot path on GB300.
 
-One step = one whole integration of the workload to its final time T, first with the
-adaptive EE2 scheme (Fig. 4, m_max = 30) and then with the adaptive LIM scheme (Fig. 3),
-both from the same seeded initial state already resident in HBM.  Metric: grid-point
-operator applications per second = N x (A_hat products + right-hand-side evaluations) /
-time, with the time to T of each scheme reported beside it.
+Default workload: 3D periodic 512^3 (134M unknowns), eps = 0.01, u0 U[-0.05, 0.05] zero
+mean, adaptive EE2 (Fig. 4, m_max = 30) and adaptive LIM (Fig. 3), tol 1e-6, tau0 = 1e-7, to
+T = 1e-4.  One step = one whole integration of the workload to T with each scheme, from the
+same seeded state already resident in HBM, both in mixed precision: EE2 with an FP32 Krylov
+basis and stencils (FP64 state, reductions, projected phi and control), LIM with its
+iterations on the FP32 increment (FP64 state, f(y^n), bound and control; a step whose
+rounding growth (tau lambda_max)^2 is too large runs in FP64).  Metric: grid-point operator
+applications per second = N x (A_hat products + right-hand-side evaluations) / time, with
+the time to T of each scheme beside it, and each scheme against the plain FP64 method on
+the same grid (time and error at T).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload c1_2d1024_adaptive]
+                    [--workload c4_3d512_adaptive | c1_2d1024_adaptive | c2_3d256_adaptive | c3_batch256]
 
 N > 1 runs under torchrun: every rank integrates its own independently seeded instance
 (replicas of the single-GPU workload, weak scaling) and rank 0 prints the JSON line.
@@ -18,6 +23,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -30,13 +36,14 @@ METRIC = "CH grid-pt updates/s & time-to-T (EE, LIM): mixed/batched vs FP64, ≤
 UNIT = "grid-pt operator applications/s"
 L2_BYTES = 129 * 2 ** 20
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2.07 GHz
-FP64_ISSUE_PEAK = 152 * 2 * 2.07e9              # FP64-pipe instructions/s
-FP64_PEAK_TFLOPS = 2 * FP64_ISSUE_PEAK / 1e12   # FMA = 2 flop
+DEFAULT_WORKLOAD = "c4_3d512_adaptive"
 try:
-    HBM_GBS = json.load(open(PEAKS_FILE))["hbm_gbs"]
+    HBM_GBS, HBM_SOURCE = json.load(open(PEAKS_FILE))["hbm_gbs"], "measured"
 except Exception:
-    HBM_GBS = 6800.0                            # fallback when the measured file is absent
+    HBM_GBS, HBM_SOURCE = 6800.0, "fallback"     # the profiling recipe's fallback copy bandwidth
+# DRAM traffic per algorithmic byte of the dominant kernel, from the ncu capture summarised
+# in this file (None when the kernel changed after the capture)
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_arnoldi_gmgs_3d_mixed.md")
 
 
 def parse():
@@ -45,25 +52,34 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c1_2d1024_adaptive")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--no-roofline", action="store_true",
-                    help="skip the per-kernel timing after the timed region (launch-list runs)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--t-final", type=float, default=None,
-                    help="integrate to this time instead of the workload's T (profiling runs only)")
+                    help="integrate to this time instead of the workload's T (short runs)")
     return ap.parse_args()
 
 
 def workload_desc(name, wl):
-    if wl["dim"] == 2:
-        grid = f"2D periodic {wl['n']}x{wl['n']}"
-    else:
-        grid = f"3D periodic {wl['n']}^3"
+    if name.startswith("c3"):
+        from paper_2502_14589_gb300 import inputs
+        return (f"batch of {wl['count']} 2D periodic instances, sides from {list(inputs.BATCH_SIDES)}, "
+                f"eps U[0.01,0.05], u0 U[{wl['lo']},{wl['hi']}] zero-mean, adaptive EE2(m_max={wl['mmax']}) "
+                f"tol {wl['tol']} to T={wl['T']}")
+    grid = f"2D periodic {wl['n']}x{wl['n']}" if wl["dim"] == 2 else f"3D periodic {wl['n']}^3"
     return (f"{grid} unit domain, eps={wl['eps']}, u0 U[{wl['lo']},{wl['hi']}] zero-mean"
             f"{'+' + str(wl['mean']) if wl['mean'] else ''}, adaptive EE2(m_max={wl['mmax']}) and LIM, "
-            f"tol={wl['tol']}, tau0={wl['tau0']}, T={wl['T']}, FP64")
+            f"tol={wl['tol']}, tau0={wl['tau0']}, T={wl['T']}")
+
+
+def host_cpu():
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "arch": platform.machine()}
 
 
 # ---------------------------------------------------------------------------------------
@@ -118,26 +134,48 @@ def parse_clock_samples(text):
             "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def profile_traffic_ratio():
+    """DRAM bytes per algorithmic byte of the dominant kernel from its ncu summary (a line
+    `dram_per_algorithmic_byte: R`), or None."""
+    try:
+        for line in open(TRAFFIC_PROFILE):
+            if line.strip().startswith("dram_per_algorithmic_byte:"):
+                return float(line.split(":", 1)[1].split()[0])
+    except (OSError, ValueError, IndexError):
+        pass
+    return None
+
+
 # ---------------------------------------------------------------------------------------
 # reference arm / CPU baseline: the plain C oracle on the host
 # ---------------------------------------------------------------------------------------
-def oracle_sample(wl, seed, steps_per_scheme):
-    """Bounded sample of the workload on the oracle: the first `steps_per_scheme` steps of
-    each adaptive scheme.  Returns (operator applications, seconds)."""
-    import numpy as np  # noqa: F401
+SAMPLE_POINTS = 8_400_000     # points of the oracle's sample slab
+
+
+def oracle_sample(wl, seed, y0=None, budget_s=5.0):
+    """Bounded sample of the workload on the oracle: f(y) of Eq. (IVP), one grid-wide
+    operator application as the metric counts them, on a slab of the workload's initial
+    state (its first planes in 3D, rows in 2D, at most SAMPLE_POINTS points, as a periodic
+    grid of that extent; the arithmetic per point is the workload's), repeated until
+    budget_s seconds have passed.  Returns (operator applications, seconds, slab shape)."""
+    import numpy as np
     from oracle import oracle
     from paper_2502_14589_gb300 import inputs
     n = [wl["n"]] * wl["dim"]
-    g = oracle.Grid(wl["dim"], n, wl["eps"])
-    y0 = inputs.initial_state(n, seed, wl["lo"], wl["hi"], wl["mean"])
+    if y0 is None:
+        y0 = inputs.initial_state(n, seed, wl["lo"], wl["hi"], wl["mean"])
+    plane = int(np.prod(n[:-1]))
+    last = max(1, min(n[-1], SAMPLE_POINTS // plane))
+    slab = n[:-1] + [last]
+    ys = np.ascontiguousarray(y0[:plane * last])
+    g = oracle.Grid(wl["dim"], slab, wl["eps"])
     ops, secs = 0, 0.0
-    for scheme in ("ee2", "lim"):
+    while secs < budget_s or ops == 0:
         t0 = time.perf_counter()
-        rc, y, t, st, rec = oracle.integrate(g, y0, scheme, True, wl["T"], wl["tau0"], tol=wl["tol"],
-                                             mmax=wl["mmax"], max_steps=steps_per_scheme, max_rec=16)
+        oracle.rhs(g, ys)
         secs += time.perf_counter() - t0
-        ops += g.N * (st["matvecs"] + st["rhs_evals"])
-    return ops, secs
+        ops += g.N
+    return ops, secs, slab
 
 
 def run_reference(args, rank, world):
@@ -147,16 +185,17 @@ def run_reference(args, rank, world):
         return
     from oracle import oracle
     oracle.build()
-    sps = 2
+    n = [wl["n"]] * wl["dim"]
+    y0 = inputs.initial_state(n, 0, wl["lo"], wl["hi"], wl["mean"])
     for _ in range(args.warmup):
-        oracle_sample(wl, 0, sps)
+        oracle_sample(wl, 0, y0, budget_s=1.0)
     tot_ops, tot_s = 0, 0.0
-    for k in range(args.steps):
-        ops, s = oracle_sample(wl, 0, sps)
+    for _ in range(args.steps):
+        ops, s, slab = oracle_sample(wl, 0, y0)
         tot_ops += ops; tot_s += s
     value = tot_ops / tot_s
-    sample = (f"first {sps} adaptive EE2 steps + first {sps} adaptive LIM steps of the workload "
-              f"per bench step, single-threaded C oracle")
+    sample = (f"per bench step: f(y) of Eq. (IVP) on a {'x'.join(map(str, slab))} slab of the workload's "
+              f"initial state (the same spacing, eps and values), repeated for >= 5 s, single-threaded C oracle")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
@@ -164,84 +203,111 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": {"workload": workload_desc(args.workload, wl), "global_batch": 1,
                    "parallelism": "replicas (rank 0 only runs the oracle)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
 # ---------------------------------------------------------------------------------------
-# batched workload: many independent instances of uneven size in one launch sequence
+# batched workload: many independent instances of uneven size in one graph launch
 # ---------------------------------------------------------------------------------------
-def run_batch_workload(args, rank, world, dist):
+def batch_compare(wl, rank, dist, T=None, warmup=1, steps=1, plain=True):
+    """The batch of independent 2D instances to T: mixed precision batched (one graph launch
+    per integration), FP64 batched, and the plain FP64 method (one grid per instance, one
+    instance after another).  Times are CUDA events on the stream around each integration."""
     import numpy as np
     import torch
-    from paper_2502_14589_gb300 import build, ch, inputs, replicas
-    build.build()
-    wl = dict(inputs.WORKLOADS[args.workload])
-    if args.t_final is not None:
-        wl["T"] = args.t_final
+    from paper_2502_14589_gb300 import ch, inputs, replicas
+    T = wl["T"] if T is None else T
     count = wl["count"]
     sides, eps = inputs.batch_descriptors(count, seed=0)
     y0s = [inputs.initial_state((int(n), int(n)), replicas.batch_instance_seed(rank, i), wl["lo"], wl["hi"])
            for i, n in enumerate(sides)]
     Ns = np.array([int(n) * int(n) for n in sides])
     stream = torch.cuda.current_stream()
-    out = {}
-    for prec, name in ((ch.CH_MIXED, "mixed"), (ch.CH_FP64, "fp64")):
+    prm = ch.make_params("ee2", True, T, wl["tau0"], wl["tol"], wl["mmax"])
+    out, ys = {}, {}
+    for prec, name in ((ch.CH_MIXED, "mixed_batched"), (ch.CH_FP64, "fp64_batched")):
         h = ch.ch_create_batch(2, [int(n) for n in sides], list(eps), prec, wl["mmax"], stream)
         offs, chunk = ch.ch_batch_layout(h, count)
         y0 = torch.zeros(offs[-1], dtype=torch.float64, device="cuda")
         for i in range(count):
             y0[offs[i]:offs[i] + Ns[i]] = torch.from_numpy(y0s[i]).cuda()
         y = torch.empty_like(y0)
-        prm = ch.make_params("ee2", True, wl["T"], wl["tau0"], wl["tol"], wl["mmax"])
-        reps = args.steps if name == "mixed" else 1
-        for _ in range(args.warmup if name == "mixed" else 1):
+        for _ in range(warmup):
             y.copy_(y0); ch.ch_integrate_batch(h, prm, y, count)
-        torch.cuda.synchronize()
-        ms, ops = 0.0, 0
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        for _ in range(reps):
+        ms, ops, launches = 0.0, 0, 0
+        for _ in range(steps):
             y.copy_(y0)
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            l0 = ch.ch_batch_kernel_launches(h)
             e0.record(stream)
             st = ch.ch_integrate_batch(h, prm, y, count)
             e1.record(stream); e1.synchronize()
             ms += e0.elapsed_time(e1)
+            launches += ch.ch_batch_kernel_launches(h) - l0
             ops += int(sum(Ns[i] * (st[i]["matvecs"] + st[i]["rhs_evals"]) for i in range(count)))
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        ms, ops = replicas.combine(dist, ms, ops, "cuda")
         yh = y.cpu().numpy()
-        out[name] = {"ms": ms / reps, "value": ops / (ms * 1e-3), "chunk_len": chunk,
-                     "steps_max": max(x["steps"] for x in st), "steps_sum": sum(x["steps"] for x in st),
-                     "y": [yh[offs[i]:offs[i] + Ns[i]] for i in range(count)],
-                     "launches": ch.ch_batch_kernel_launches(h)}
+        ys[name] = [yh[offs[i]:offs[i] + Ns[i]] for i in range(count)]
+        out[name] = {"ms_to_T": ms / steps, "value": ops / (ms * 1e-3), "chunk_len": chunk,
+                     "batch_steps": max(x["steps"] for x in st), "kernel_launches": launches // steps}
         ch.ch_destroy_batch(h)
-    errs = [np.linalg.norm(a - b) / np.linalg.norm(b) for a, b in zip(out["mixed"]["y"], out["fp64"]["y"])]
-    for k in out:
-        out[k].pop("y")
+    if plain:
+        ms, ops, yp = 0.0, 0, []
+        for i, n in enumerate(sides):
+            G = ch.Grid(2, (int(n), int(n)), float(eps[i]), ch.CH_FP64, wl["mmax"], stream)
+            y = torch.from_numpy(y0s[i]).cuda()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = ch.ch_integrate(G.h, prm, y)
+            e1.record(stream); e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            ops += int(Ns[i]) * (st["matvecs"] + st["rhs_evals"])
+            yp.append(y.cpu().numpy())
+            G.close()
+        out["fp64_plain"] = {"ms_to_T": ms, "value": ops / (ms * 1e-3),
+                             "method": "one FP64 grid per instance, integrated one after another"}
+    ref = ys["fp64_batched"]
+    errs = [np.linalg.norm(a - b) / np.linalg.norm(b) for a, b in zip(ys["mixed_batched"], ref)]
+    out["mixed_batched_vs_fp64_batched"] = {"speedup": out["fp64_batched"]["ms_to_T"] / out["mixed_batched"]["ms_to_T"],
+                                            "max_rel_err_at_T": float(max(errs)),
+                                            "median_rel_err_at_T": float(np.median(errs))}
+    if plain:
+        out["mixed_batched_vs_fp64_plain"] = {"speedup": out["fp64_plain"]["ms_to_T"] / out["mixed_batched"]["ms_to_T"]}
+    out["grid_points"] = int(Ns.sum())
+    out["T"] = T
+    return out
+
+
+def run_batch_workload(args, rank, world, dist):
+    import torch
+    from paper_2502_14589_gb300 import build, inputs, replicas
+    build.build()
+    wl = dict(inputs.WORKLOADS[args.workload])
+    if args.t_final is not None:
+        wl["T"] = args.t_final
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    out = batch_compare(wl, rank, dist, warmup=args.warmup, steps=args.steps)
+    ms, ops = replicas.combine(dist, out["mixed_batched"]["ms_to_T"] * args.steps,
+                               out["mixed_batched"]["value"] * out["mixed_batched"]["ms_to_T"] * 1e-3 * args.steps,
+                               "cuda")
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": out["mixed"]["value"], "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["mixed"]["ms"],
+            "metric": METRIC, "value": ops / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed",
             "data": "synthetic",
-            "config": {"workload": f"batch of {count} 2D periodic instances, sides from {list(inputs.BATCH_SIDES)}, "
-                                   f"eps U[0.01,0.05], u0 U[{wl['lo']},{wl['hi']}] zero-mean, adaptive EE2(m_max="
-                                   f"{wl['mmax']}) tol {wl['tol']} to T={wl['T']}, FP32 Krylov basis/stencils, FP64 "
-                                   f"reductions/phi/control", "global_batch": count, "grid_points": int(Ns.sum())},
-            "batch": out, "mixed_vs_fp64": {"speedup": out["fp64"]["ms"] / out["mixed"]["ms"],
-                                             "max_rel_err_at_T": float(max(errs)),
-                                             "median_rel_err_at_T": float(np.median(errs))},
+            "config": {"workload": workload_desc(args.workload, wl), "global_batch": wl["count"],
+                       "grid_points": out["grid_points"], "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "batch": out,
         }), flush=True)
 
 
 # ---------------------------------------------------------------------------------------
-# GPU arm
+# GPU arm: one grid, EE2 in mixed precision and LIM in FP64 to T
 # ---------------------------------------------------------------------------------------
 def main():
     args = parse()
@@ -282,21 +348,21 @@ def main():
     y = torch.empty_like(y0)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    G = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_FP64, wl["mmax"], stream)
+    Gm = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_MIXED, wl["mmax"], stream)     # the timed step
+    Gd = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_FP64, wl["mmax"], stream)      # the plain FP64 method
     prm = {s: ch.make_params(s, True, wl["T"], wl["tau0"], wl["tol"], wl["mmax"]) for s in ("ee2", "lim")}
+    grid_of = {"ee2": Gm, "lim": Gm}
+    y_at_T = {s: torch.empty_like(y0) for s in ("ee2", "lim")}
 
-    y_ee2 = torch.empty_like(y0)              # EE2 solution at T of the last step
-
-    def one_step(yin_dev, record=None):
+    def one_step(yin, record=None):
         stats = {}
         for s in ("ee2", "lim"):
-            y.copy_(yin_dev)
+            y.copy_(yin)
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            stats[s] = ch.ch_integrate(G.h, prm[s], y)
+            stats[s] = ch.ch_integrate(grid_of[s].h, prm[s], y)
             e1.record(stream)
-            if s == "ee2":
-                y_ee2.copy_(y)
+            y_at_T[s].copy_(y)
             if record is not None:
                 record[s].append((e0, e1, stats[s]))
         return stats
@@ -306,8 +372,9 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region: K steps, events per step, L2 flushed between steps --------------
-    ch.ch_timing_start(G.h, None)           # per-class launch counts, no per-kernel events
-    launches0 = ch.ch_kernel_launches(G.h)
+    for G in (Gm, Gd):
+        ch.ch_timing_start(G.h, None)       # per-class launch counts, no per-kernel events
+    launches0 = ch.ch_kernel_launches(Gm.h) + ch.ch_kernel_launches(Gd.h)
     clocks = ClockSampler()
     if rank == 0:
         clocks.start()
@@ -315,7 +382,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     step_ms, ops, rec = [], 0, {"ee2": [], "lim": []}
-    for k in range(args.steps):
+    for _ in range(args.steps):
         flush.zero_()
         ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
@@ -329,136 +396,130 @@ def main():
     if dist is not None:
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
-    launches = ch.ch_kernel_launches(G.h) - launches0
-    _, _, counts = ch.ch_timing_read(G.h)
+    launches = ch.ch_kernel_launches(Gm.h) + ch.ch_kernel_launches(Gd.h) - launches0
+    counts = {}
+    for G in (Gm, Gd):
+        for k, v in ch.ch_timing_read(G.h)[2].items():
+            counts[k] = counts.get(k, 0) + v
     total_ms, ops = replicas.combine(dist, sum(step_ms), ops, dev)
     value = ops / (total_ms * 1e-3)
     ttt = {}
-    for s in ("ee2", "lim"):
+    for s, prec in (("ee2", "mixed"), ("lim", "mixed")):
         ms = [e0.elapsed_time(e1) for e0, e1, _ in rec[s]]
         st = rec[s][-1][2]
-        ttt[s] = {"ms": sum(ms) / len(ms), "steps": st["steps"], "matvecs": st["matvecs"],
-                  "rhs_evals": st["rhs_evals"], "phi_evals": st["phi_evals"],
-                  "tau_shrinks": st["tau_shrinks"],
+        ttt[s] = {"precision": prec, "ms": sum(ms) / len(ms), "steps": st["steps"], "matvecs": st["matvecs"],
+                  "rhs_evals": st["rhs_evals"], "phi_evals": st["phi_evals"], "tau_shrinks": st["tau_shrinks"],
                   "ops_per_s": N * (st["matvecs"] + st["rhs_evals"]) / (sum(ms) / len(ms) * 1e-3)}
 
-    # ---- mixed precision on the same instance: time to T and error at T against FP64 ----
-    mixed = None
-    if not args.no_mixed:
-        y_fp64 = y_ee2.clone()                            # FP64 EE2 at T from the timed step
-        Gm = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_MIXED, wl["mmax"], stream)
-        ym = torch.empty_like(y0)
-        ym.copy_(y0)
-        pw = ch.make_params("ee2", True, wl["T"] / 10, wl["tau0"], wl["tol"], wl["mmax"])
-        ch.ch_integrate(Gm.h, pw, ym)                     # warm-up (graph capture)
-        ym.copy_(y0)
+    # ---- the plain FP64 method on the same grid: time to T and the mixed runs' error at T ----
+    mixed_vs_fp64 = {}
+    for s in ("ee2", "lim"):
+        y.copy_(y0)
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        stm = ch.ch_integrate(Gm.h, prm["ee2"], ym)
+        st64 = ch.ch_integrate(Gd.h, prm[s], y)
         e1.record(stream); e1.synchronize()
-        ms_m = e0.elapsed_time(e1)
-        err = float(torch.linalg.norm(ym - y_fp64) / torch.linalg.norm(y_fp64))
-        mixed = {"ee2_ms_to_T": ms_m, "ee2_speedup_vs_fp64": ttt["ee2"]["ms"] / ms_m,
-                 "ee2_rel_err_at_T_vs_fp64": err, "steps": stm["steps"], "matvecs": stm["matvecs"],
-                 "ops_per_s": N * (stm["matvecs"] + stm["rhs_evals"]) / (ms_m * 1e-3),
-                 "mass_drift": float(abs(ym.mean() - y0.mean()))}
-        if not args.no_roofline:        # one Arnoldi iteration (j = 10) on the FP32 basis
-            mixed["arnoldi_j10_us"] = ch.ch_bench_kernel(Gm.h, "arnoldi", 50)["avg_us"]
-        Gm.close()
+        ms64 = e0.elapsed_time(e1)
+        mixed_vs_fp64[s] = {"fp64_ms_to_T": ms64, "mixed_ms_to_T": ttt[s]["ms"], "speedup": ms64 / ttt[s]["ms"],
+                            "rel_err_at_T_vs_fp64": float(torch.linalg.norm(y_at_T[s] - y) / torch.linalg.norm(y)),
+                            "fp64_steps": st64["steps"], "mixed_steps": ttt[s]["steps"],
+                            "mixed_mass_drift": float(abs(y_at_T[s].mean() - y0.mean()))}
 
-    # ---- end to end through the C ABI with host buffers ----------------------------------
-    e2e = None
-    if not args.no_e2e:
-        y_host = torch.from_numpy(y0_host.copy()).pin_memory()
-        out_host = torch.empty(N, dtype=torch.float64).pin_memory()
-        e2e_ops, e2e_ms = 0, 0.0
-        for k in range(max(1, args.steps // 2)):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for s in ("ee2", "lim"):
-                y.copy_(y_host, non_blocking=True)
-                st = ch.ch_integrate(G.h, prm[s], y)
-                out_host.copy_(y, non_blocking=True)
-                e2e_ops += N * (st["matvecs"] + st["rhs_evals"])
-            e1.record(stream)
-            e1.synchronize()
-            e2e_ms += e0.elapsed_time(e1)
-        e2e = {"value": e2e_ops / (e2e_ms * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": 2 * N * 8}
+    # ---- end to end through the C ABI with host buffers (one step) ---------------------------
+    y_host = torch.from_numpy(y0_host.copy()).pin_memory()
+    out_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_ops = 0
+    for s in ("ee2", "lim"):
+        y.copy_(y_host, non_blocking=True)
+        st = ch.ch_integrate(grid_of[s].h, prm[s], y)
+        out_host.copy_(y, non_blocking=True)
+        e2e_ops += N * (st["matvecs"] + st["rhs_evals"])
+    e1.record(stream); e1.synchronize()
+    e2e = {"value": e2e_ops / (e0.elapsed_time(e1) * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": 2 * N * 8}
 
-    # ---- per-class kernel table: each class timed on the workload grid with CUDA events on
-    # the grid's stream around a graph of 200 back-to-back launches (Arnoldi iteration at j = 10)
-    kernels = {}
-    classes = ("arnoldi", "tstage", "wstage", "mgs", "resid1", "lim2", "rhs1", "rhs2")
-    for cls in (() if args.no_roofline else classes):
-        if counts[cls] == 0:
-            continue                     # not launched in the timed region on this grid
-        kb = ch.ch_bench_kernel(G.h, cls, 200)
-        dur = kb["avg_us"] * 1e-6
-        kernels[cls] = {"launches": counts[cls], "avg_us": kb["avg_us"],
-                        "est_share_s": counts[cls] * dur,
-                        "gbs": kb["bytes"] / dur / 1e9, "tflops": kb["flops"] / dur / 1e12,
-                        "fp64_issue_frac": kb["fp64_instr"] / dur / FP64_ISSUE_PEAK,
-                        "bytes": kb["bytes"], "flops": kb["flops"], "fp64_instr": kb["fp64_instr"]}
-    # ---- roofline of the dominant kernel, measured live: every launch of its class timed
-    # with CUDA events on the grid's stream over the first twentieth of the workload's run
-    # (t in [0, T/20], the same kernels and Krylov dimensions as the timed region; CUDA
-    # graphs are off while launches are timed), with the algorithmic work of each launch
-    # summed by the library (flops and bytes per point times the points of the launch)
-    roof, live = None, {}
-    if kernels:
-        for cls, scheme in (("arnoldi", "ee2"), ("lim2", "lim")):
-            if cls not in kernels:
-                continue
-            y.copy_(y0)
-            ch.ch_timing_start(G.h, cls)
-            seg = ch.make_params(scheme, True, wl["T"] / 20, wl["tau0"], wl["tol"], wl["mmax"])
-            ch.ch_integrate(G.h, seg, y)
-            ms, nt, _ = ch.ch_timing_read(G.h)
-            fl, by = ch.ch_timing_work(G.h)
-            ch.ch_timing_start(G.h, None)
-            if nt > 0 and ms > 0:
-                live[cls] = {"launches": nt, "avg_us": 1e3 * ms / nt, "tflops": fl / (ms * 1e-3) / 1e12,
-                             "gbs": by / (ms * 1e-3) / 1e9, "flops_per_launch": fl / nt,
-                             "bytes_per_launch": by / nt}
-        dom = max(kernels, key=lambda c: kernels[c]["est_share_s"])
-        if dom in live:
-            kl = live[dom]
-            roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": kl["tflops"],
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kl["tflops"] / FP64_PEAK_TFLOPS,
-                    "traffic": None,
-                    "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 pipe)",
-                    "measured": f"{kl['launches']} launches timed live over t in [0, T/20]",
-                    "avg_launch_us": kl["avg_us"], "algorithmic_flops_per_launch": kl["flops_per_launch"],
-                    "algorithmic_bytes_per_launch": kl["bytes_per_launch"], "achieved_gbs": kl["gbs"],
-                    "hbm_frac_of_measured": kl["gbs"] / HBM_GBS}
+    # ---- roofline of the dominant kernel, measured live: every launch of the FP32 Arnoldi
+    # iteration (Gram-corrected, HBM-bound) timed with CUDA events on the grid's stream over
+    # t in [0, T/20] of the same workload (graphs off while launches are timed); the library
+    # sums each launch's algorithmic bytes and flops from its Krylov dimension and N.  The
+    # FP64 LIM kernels (FP64-issue bound) are timed the same way against the measured FP64 peak.
+    fp64_peak = ch.ch_probe_fp64_peak(stream)
+    live = {}
+    for cls, scheme, G in (("arnoldi", "ee2", Gm), ("lim2", "lim", Gm), ("lim2", "lim", Gd), ("resid1", "lim", Gd)):
+        key = cls if G is Gm else cls + "_fp64"
+        y.copy_(y0)
+        ch.ch_timing_start(G.h, cls)
+        ch.ch_integrate(G.h, ch.make_params(scheme, True, wl["T"] / 20, wl["tau0"], wl["tol"], wl["mmax"]), y)
+        ms, nt, _ = ch.ch_timing_read(G.h)
+        fl, by = ch.ch_timing_work(G.h)
+        ch.ch_timing_start(G.h, None)
+        if nt > 0 and ms > 0:
+            live[key] = {"launches": nt, "avg_us": 1e3 * ms / nt, "gbs": by / (ms * 1e-3) / 1e9,
+                         "tflops": fl / (ms * 1e-3) / 1e12, "bytes_per_launch": by / nt,
+                         "flops_per_launch": fl / nt, "launches_in_timed_step": counts.get(cls, 0) // max(1, args.steps)}
+    roof = None
+    if "arnoldi" in live:
+        kl = live["arnoldi"]
+        ratio = profile_traffic_ratio()
+        roof = {"kernel": "k_arnoldi_gmgs", "bound": "hbm", "achieved": kl["gbs"], "peak": HBM_GBS, "unit": "GB/s",
+                "frac": kl["gbs"] / HBM_GBS,
+                "traffic": None if ratio is None else ratio * kl["bytes_per_launch"],
+                "peak_source": f"{HBM_SOURCE} (MEASURED_PEAKS.json hbm_gbs)" if HBM_SOURCE == "measured" else "fallback",
+                "measured": f"{kl['launches']} launches timed live over t in [0, T/20]",
+                "avg_launch_us": kl["avg_us"], "algorithmic_bytes_per_launch": kl["bytes_per_launch"],
+                "algorithmic_flops_per_launch": kl["flops_per_launch"],
+                "est_share_of_step": kl["avg_us"] * 1e-3 * kl["launches_in_timed_step"] / (total_ms / args.steps)}
+    fp64_kernels = {c: {**live[c], "frac_of_measured_fp64": live[c]["tflops"] / fp64_peak}
+                    for c in ("lim2_fp64", "resid1_fp64") if c in live}
+    # the dominant kernel in isolation at a fixed Krylov dimension (j = 10): 20 back-to-back
+    # launches in a CUDA graph, events around it (an NVTX range "ch_bench_kernel" marks them)
+    kb = ch.ch_bench_kernel(Gm.h, "arnoldi", 20)
+    isolated = {"kernel": "k_arnoldi_gmgs", "j": 10, "avg_us": kb["avg_us"],
+                "algorithmic_bytes": kb["bytes"], "gbs": kb["bytes"] / (kb["avg_us"] * 1e-6) / 1e9,
+                "frac_of_hbm": kb["bytes"] / (kb["avg_us"] * 1e-6) / 1e9 / HBM_GBS}
+
+    # ---- the batched workload (256 2D instances of uneven size to T = 1e-4), once: mixed
+    # precision batched against FP64 batched and the plain FP64 method instance by instance
+    batch = None
+    if args.workload == DEFAULT_WORKLOAD and args.t_final is None:
+        Gm.close(); Gd.close()
+        del flush
+        torch.cuda.empty_cache()
+        batch = batch_compare(dict(inputs.WORKLOADS["c3_batch256"]), rank, dist)
+        batch["workload"] = workload_desc("c3_batch256", inputs.WORKLOADS["c3_batch256"])
 
     # ---- CPU baseline (oracle on a bounded sample, rank 0 only, N = 1) -----------------
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1:
         from oracle import oracle
         oracle.build()
-        c_ops, c_s = oracle_sample(wl, 0, 12)
-        cpu = {"value": c_ops / c_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first 12 adaptive EE2 steps + first 12 adaptive LIM steps of the same "
-                         f"workload (seed 0), {c_s:.1f} s single-threaded on the host"}
+        c_ops, c_s, slab = oracle_sample(wl, 0, y0_host, budget_s=15.0)
+        cpu = {"value": c_ops / c_s, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+               "sample": f"f(y) of Eq. (IVP) on a {'x'.join(map(str, slab))} slab of the workload's initial "
+                         f"state (same spacing, eps, values), {c_ops // (int(np.prod(slab)))} evaluations in "
+                         f"{c_s:.1f} s single-threaded on the host"}
 
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(args.workload, wl), "global_batch": world,
-                       "grid_points": N, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "flushed (256 MiB write) before every timed step"},
-            "time_to_T": ttt, "e2e": e2e, "gpu_launches": launches, "launches_by_kernel": counts,
-            "mixed": mixed, "roofline": roof, "kernels": kernels, "kernels_live": live, "hbm_peak_gbs": HBM_GBS, "cpu_baseline": cpu,
-            "clocks": clk,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed", "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload, wl), "global_batch": world, "grid_points": N,
+                       "step": "EE2 to T, then LIM to T, both mixed precision, from the same state",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed (256 MiB write) before every timed step; every vector of the workload exceeds L2"},
+            "time_to_T": ttt, "mixed_vs_fp64": mixed_vs_fp64, "e2e": e2e, "gpu_launches": launches,
+            "launches_by_kernel": counts, "roofline": roof, "kernels_live": live, "fp64_kernels": fp64_kernels,
+            "dominant_isolated": isolated,
+            "fp64_peak_tflops": {"measured": fp64_peak, "how": "ch_probe_fp64_peak: FMA chains from registers"},
+            "hbm_peak_gbs": HBM_GBS, "cpu_baseline": cpu, "clocks": clk, "batch_c3": batch,
         }
         print(json.dumps(out), flush=True)
-    G.close()
+    Gm.close(); Gd.close()
     if dist is not None:
         dist.destroy_process_group()
 

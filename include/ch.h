@@ -298,10 +298,11 @@ ch_status ch_energy_mass_noalloc(int dim, const int64_t n[3], double eps, const 
                                  double *out, void *cuda_stream);
 
 /* Measured FP64 FMA rate of the current GPU in TFLOP/s (an FMA counts 2): independent FMA
- * chains from registers on a full grid, timed with CUDA events on cuda_stream (best of three
- * launches after a warm-up).  No counterpart in the paper: it is the roofline denominator of
- * the FP64 kernels, which are bound by FP64 issue on GB300.  Allocates and frees a small
- * output buffer; synchronises the stream.                                                 */
+ * chains from registers on a grid of all resident blocks, the best over a few shapes (4, 8
+ * or 16 chains per thread, 256 or 1024 threads per block), each timed with CUDA events on
+ * cuda_stream after a warm-up launch.  No counterpart in the paper: it is the roofline
+ * denominator of the FP64 kernels, which are bound by FP64 issue on GB300.  Allocates and
+ * frees a small output buffer; synchronises the stream.                                   */
 ch_status ch_probe_fp64_peak(void *cuda_stream, double *tflops);
 
 /* Message of the last error on the calling thread ("" when none). */

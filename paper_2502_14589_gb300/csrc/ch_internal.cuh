@@ -285,6 +285,13 @@ void launch_resid2(const Launch &L, const Geom &g, const double *t, double *out)
 void launch_lim2(const Launch &L, const Geom &g, const double *t, const double *yn,
                  const double *yprev, double *ynext, double tau_a, double tau, double alpha);
 void launch_energy(const Launch &L, const Geom &g, const double *y);
+// LIM iteration of Fig. 1 on the FP32 increment d = y_prev - y^n (mixed grids): t from
+// launch_tstage<float>(d, J); d_next = ta d_prev + atau (f^n - A t), ta = alpha tau a_m,
+// atau = alpha tau (dprev == nullptr: the first iteration from d = 0); then
+// y_next = y0 + d - mean(d).
+void launch_lim32(const Launch &L, const Geom &g, const float *t, const double *fn,
+                  const float *dprev, float *dnext, double ta, double atau);
+void launch_add_increment(const Launch &L, int64_t N, const double *y0, const float *d, double *ynext);
 // Face mobilities mf_a = s_a (M_i + M_{i+e_a}) / 2 (and FP32 copies when mff[a] != nullptr)
 // from nodal values M; ||A_hat||_1 by explicit columns into red[4] (Neumann or variable-
 // mobility grids, where the periodic closed form does not hold).

@@ -1354,6 +1354,45 @@ k_lim2(Geom g, const double *__restrict__ t, const double *__restrict__ yn,
     })
 }
 
+// ---------------------------------------------------------------------------------------
+// LIM iteration of Fig. 1 in increment form for mixed-precision grids.  With
+// y_prev = y^n + d and the identity g_hat - A_hat y^n = f(y^n) (Eq. A_g), the update reads
+//     d_next = alpha (tau a_m d + tau (f^n - A_hat d)),   y^{n+1} = y^n + d_final,
+// the same iterate as Fig. 1's, with rounding relative to the increment d, not to y.  Stage 1
+// is k_tstage<float> on d (FP32 difference form with J); lim32: A t in FP32 and the update,
+// f^n read in FP64.  d_prev == nullptr is the first iteration (d = 0, a_1 = 0).
+// ---------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_lim32(Geom g, const float *__restrict__ t, const double *__restrict__ fn,
+        const float *__restrict__ dprev, float *__restrict__ dnext, float ta, float atau) {
+    const float c1 = (float)g.s[0], c2 = (float)g.s[1], c3 = (float)g.s[2];
+    GRID_LOOP2(g.N, {
+        float ad = 0.f;
+        if (dprev) ad = stage2_at<DIM, float>(g, t, i, 0.f, c1, c2, c3, 1.f);      // A_hat d
+        const float r = (float)fn[i] - ad;
+        dnext[i] = dprev ? fmaf(ta, dprev[i], atau * r) : atau * r;
+    })
+}
+
+// Sum of an FP32 increment (compensated, into red[6]) and y_next = y0 + (d - mean(d)): the
+// increment of a LIM step has zero sum in exact arithmetic (columns of A sum to zero, Eq. m),
+// so the FP32 rounding's share of the mass is removed.
+__global__ void __launch_bounds__(kThreads)
+k_sum32(int64_t N, const float *__restrict__ d, double *partials, unsigned int *ticket, Ctrl *ctrl) {
+    DotAcc<float> acc;
+    GRID_LOOP(i, N) acc.add_value(d[i]);
+    double tot1[1] = {acc.value()};
+    grid_sum<1>(tot1, partials, ticket, [&](double (&tot)[1]) { ctrl->red[6] = tot[0]; });
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_add_increment(int64_t N, const double *__restrict__ y0, const float *__restrict__ d,
+                double *__restrict__ ynext, const Ctrl *ctrl) {
+    const double mean = ctrl->red[6] / (double)N;
+    GRID_LOOP(i, N) ynext[i] = y0[i] + ((double)d[i] - mean);
+}
+
 // Energy of Eq. (Ediscr) (periodic forward differences) and mass: red[6], red[7] (unscaled
 // sums; the host multiplies by h^d).
 template <int DIM>
@@ -1646,6 +1685,23 @@ void launch_lim2(const Launch &L, const Geom &g, const double *t, const double *
     scope.work((5.0 + 3.0 * g.dim) * g.N, 32.0 * g.N);      // stage 2 + update; t, yn, yprev, ynext
     if (g.dim == 3) k_lim2<3><<<L.blocks, kThreads, 0, L.stream>>>(g, t, yn, yprev, ynext, tau_a, tau, alpha);
     else k_lim2<2><<<L.blocks, kThreads, 0, L.stream>>>(g, t, yn, yprev, ynext, tau_a, tau, alpha);
+}
+
+void launch_lim32(const Launch &L, const Geom &g, const float *t, const double *fn,
+                  const float *dprev, float *dnext, double ta, double atau) {
+    LaunchScope scope(L, CH_K_LIM2);
+    scope.work((4.0 + 3.0 * g.dim) * g.N, 24.0 * g.N);     // stage 2 + update; t, f, d_prev, d_next
+    if (g.dim == 3) k_lim32<3><<<L.blocks, kThreads, 0, L.stream>>>(g, t, fn, dprev, dnext, (float)ta, (float)atau);
+    else k_lim32<2><<<L.blocks, kThreads, 0, L.stream>>>(g, t, fn, dprev, dnext, (float)ta, (float)atau);
+}
+
+void launch_add_increment(const Launch &L, int64_t N, const double *y0, const float *d, double *ynext) {
+    {
+        LaunchScope scope(L, CH_K_COMBINE);
+        k_sum32<<<L.blocks, kThreads, 0, L.stream>>>(N, d, L.partials, &L.ctrl->ticket[0], L.ctrl);
+    }
+    LaunchScope scope(L, CH_K_COMBINE);
+    k_add_increment<<<L.blocks, kThreads, 0, L.stream>>>(N, y0, d, ynext, L.ctrl);
 }
 
 void launch_energy(const Launch &L, const Geom &g, const double *y) {

@@ -20,7 +20,7 @@ def test_reference_arm_prints_one_contract_line_from_rank_0():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
            os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
-           "--steps", "1", "--warmup", "0"]
+           "--steps", "1", "--warmup", "0", "--workload", "c2_3d256_adaptive"]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
@@ -30,9 +30,10 @@ def test_reference_arm_prints_one_contract_line_from_rank_0():
     assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["steps"] == 1
     assert out["value"] > 0 and out["higher_is_better"] is True and out["vs_baseline"] is None
     assert out["unit"] == "grid-pt operator applications/s" and out["dtype"] == "f64"
-    assert "1024x1024" in out["config"]["workload"]
+    assert "256^3" in out["config"]["workload"]
     cb = out["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == out["value"] and cb["sample"]
+    assert cb["host"]["nproc"] >= 1 and cb["host"]["model"]
     e2e = out["e2e"]
     assert e2e["value"] == out["value"] and e2e["unit"] == out["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

@@ -105,3 +105,38 @@ def test_mixed_krylov_beyond_31_dimensions(ch, oracle):
     assert rc == 0
     assert np.linalg.norm(yg - yo) / np.linalg.norm(yo - y) < 50 * U32 * max(tu * lmax, 1.0)
     assert abs(yg.mean() - y.mean()) < 1e-13
+
+
+@pytest.mark.parametrize("dim,n,tau,eyre", [(2, (64, 64), 3e-7, 0), (2, (50, 70), 2e-6, 1), (3, (24, 20, 16), 5e-7, 0)])
+def test_mixed_lim_step_in_increment_form(ch, oracle, dim, n, tau, eyre):
+    """Fig. 1 on a mixed-precision grid runs on the FP32 increment d = y_prev - y^n (when the
+    rounding growth 3 (tau lambda_max)^2 u32 is small): the step agrees with the oracle's to
+    the FP32 bound relative to the increment, with the same p, and keeps the mass."""
+    eps = 0.05
+    y = inputs.initial_state(n, 8, -0.05, 0.05)
+    og = oracle.Grid(dim, n, eps, eyre=bool(eyre))
+    yo, po, lo, _ = oracle.lim_step(og, y, tau)
+    assert 3 * (tau * lo) ** 2 * U32 <= 1e-5          # the increment form applies
+    with ch.Grid(dim, n, eps, ch.CH_MIXED) as G:
+        yn = torch.empty(G.N, dtype=torch.float64, device="cuda")
+        p, lm = ch.ch_lim_step(G.h, dev(y), tau, yn, eyre)
+        yg = host(yn)
+    assert p == po
+    assert np.linalg.norm(yg - yo) / np.linalg.norm(yo - y) < 50 * U32 * max(3 * (tau * lo) ** 2, 1.0)
+    assert abs(yg.mean() - y.mean()) < 1e-14
+
+
+@pytest.mark.parametrize("dim,n,eps,T", [(2, (64, 64), 0.05, 2e-4), (3, (16, 16, 16), 0.05, 1e-4)])
+def test_mixed_adaptive_lim_error_at_T(ch, oracle, dim, n, eps, T):
+    """Adaptive LIM (Fig. 3) on a mixed-precision grid: every step whose tau lambda_max allows
+    it runs the FP32 increment form; the solution at T agrees with the FP64 oracle's to 1e-5
+    and the mass is kept."""
+    y0 = inputs.initial_state(n, 4, -0.05, 0.05)
+    with ch.Grid(dim, n, eps, ch.CH_MIXED) as G:
+        y = dev(y0)
+        st = ch.ch_integrate(G.h, ch.make_params("lim", True, T, 1e-8, 1e-6), y)
+        yg = host(y)
+    rc, yo, to, sto, _ = oracle.integrate(oracle.Grid(dim, n, eps), y0, "lim", True, T, 1e-8, tol=1e-6)
+    assert rc == 0 and st["t"] == T
+    assert np.linalg.norm(yg - yo) / np.linalg.norm(yo) < 1e-5
+    assert abs(yg.mean() - y0.mean()) < 1e-13
