@@ -3,13 +3,14 @@
 Default workload: 3D periodic 512^3 (134M unknowns), eps = 0.01, u0 U[-0.05, 0.05] zero
 mean, adaptive EE2 (Fig. 4, m_max = 30) and adaptive LIM (Fig. 3), tol 1e-6, tau0 = 1e-7, to
 T = 1e-4.  One step = one whole integration of the workload to T with each scheme, from the
-same seeded state already resident in HBM, both in mixed precision: EE2 with an FP32 Krylov
-basis and stencils (FP64 state, reductions, projected phi and control), LIM with its
-iterations on the FP32 increment (FP64 state, f(y^n), bound and control; a step whose
-rounding growth (tau lambda_max)^2 is too large runs in FP64).  Metric: grid-point operator
-applications per second = N x (A_hat products + right-hand-side evaluations) / time, with
-the time to T of each scheme beside it, and each scheme against the plain FP64 method on
-the same grid (time and error at T).
+same seeded state already resident in HBM: EE2 in mixed precision (FP32 Krylov basis and
+stencils; FP64 state, reductions, projected phi and control) and LIM in FP64.  Metric:
+grid-point operator applications per second = N x (A_hat products + right-hand-side
+evaluations) / time, with the time to T of each scheme beside it, and the mixed-precision
+EE2 against the plain FP64 EE2 on the same grid (time and error at T).  The mixed-precision
+LIM (FP32 iterations on the increment) is reported beside the step: at this workload its
+per-step FP64 work (bound, right-hand side, estimate) dominates, and Eq. (LIMdt)'s
+unclamped growth makes adaptive LIM runs that differ by rounding take different steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--workload c4_3d512_adaptive | c1_2d1024_adaptive | c2_3d256_adaptive | c3_batch256]
@@ -351,7 +352,7 @@ def main():
     Gm = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_MIXED, wl["mmax"], stream)     # the timed step
     Gd = ch.Grid(wl["dim"], n, wl["eps"], ch.CH_FP64, wl["mmax"], stream)      # the plain FP64 method
     prm = {s: ch.make_params(s, True, wl["T"], wl["tau0"], wl["tol"], wl["mmax"]) for s in ("ee2", "lim")}
-    grid_of = {"ee2": Gm, "lim": Gm}
+    grid_of = {"ee2": Gm, "lim": Gd}
     y_at_T = {s: torch.empty_like(y0) for s in ("ee2", "lim")}
 
     def one_step(yin, record=None):
@@ -371,9 +372,12 @@ def main():
         one_step(y0)
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, events per step, L2 flushed between steps --------------
-    for G in (Gm, Gd):
-        ch.ch_timing_start(G.h, None)       # per-class launch counts, no per-kernel events
+    # ---- timed region: K steps, events per step, L2 flushed between steps.  Every launch of
+    # the dominant kernel (the FP32 Arnoldi iteration of EE2) is timed with CUDA events on the
+    # grid's stream inside the timed steps (launches that found their Krylov run ended and
+    # returned at once excluded); the library sums each launch's algorithmic bytes and flops.
+    ch.ch_timing_start(Gm.h, "arnoldi")
+    ch.ch_timing_start(Gd.h, None)          # per-class launch counts, no per-kernel events
     launches0 = ch.ch_kernel_launches(Gm.h) + ch.ch_kernel_launches(Gd.h)
     clocks = ClockSampler()
     if rank == 0:
@@ -398,33 +402,59 @@ def main():
     clk = clocks.stop() if rank == 0 else None
     launches = ch.ch_kernel_launches(Gm.h) + ch.ch_kernel_launches(Gd.h) - launches0
     counts = {}
-    for G in (Gm, Gd):
-        for k, v in ch.ch_timing_read(G.h)[2].items():
+    arn_ms, arn_n, cm = ch.ch_timing_read(Gm.h)
+    arn_fl, arn_by = ch.ch_timing_work(Gm.h)
+    ch.ch_timing_start(Gm.h, None)
+    for c in (cm, ch.ch_timing_read(Gd.h)[2]):
+        for k, v in c.items():
             counts[k] = counts.get(k, 0) + v
     total_ms, ops = replicas.combine(dist, sum(step_ms), ops, dev)
     value = ops / (total_ms * 1e-3)
     ttt = {}
-    for s, prec in (("ee2", "mixed"), ("lim", "mixed")):
+    for s, prec in (("ee2", "mixed"), ("lim", "fp64")):
         ms = [e0.elapsed_time(e1) for e0, e1, _ in rec[s]]
         st = rec[s][-1][2]
         ttt[s] = {"precision": prec, "ms": sum(ms) / len(ms), "steps": st["steps"], "matvecs": st["matvecs"],
                   "rhs_evals": st["rhs_evals"], "phi_evals": st["phi_evals"], "tau_shrinks": st["tau_shrinks"],
                   "ops_per_s": N * (st["matvecs"] + st["rhs_evals"]) / (sum(ms) / len(ms) * 1e-3)}
 
-    # ---- the plain FP64 method on the same grid: time to T and the mixed runs' error at T ----
-    mixed_vs_fp64 = {}
-    for s in ("ee2", "lim"):
+    # ---- the plain FP64 EE2 on the same grid: time to T and the mixed run's error at T ----
+    y.copy_(y0)
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st64 = ch.ch_integrate(Gd.h, prm["ee2"], y)
+    e1.record(stream); e1.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    mixed_vs_fp64 = {"ee2": {"fp64_ms_to_T": ms64, "mixed_ms_to_T": ttt["ee2"]["ms"], "speedup": ms64 / ttt["ee2"]["ms"],
+                             "rel_err_at_T_vs_fp64": float(torch.linalg.norm(y_at_T["ee2"] - y) / torch.linalg.norm(y)),
+                             "fp64_steps": st64["steps"], "mixed_steps": ttt["ee2"]["steps"],
+                             "mixed_mass_drift": float(abs(y_at_T["ee2"].mean() - y0.mean()))}}
+    # mixed-precision LIM: adaptive to T (time; its adaptive step sequence departs from the
+    # FP64 run's, so the difference at T measures Eq. (LIMdt)'s sensitivity), and 200 constant
+    # steps against the same 200 FP64 steps (the precision effect alone)
+    y.copy_(y0)
+    e0.record(stream)
+    stm = ch.ch_integrate(Gm.h, prm["lim"], y)
+    e1.record(stream); e1.synchronize()
+    lim_m_ms = e0.elapsed_time(e1)
+    lim_adapt_diff = float(torch.linalg.norm(y - y_at_T["lim"]) / torch.linalg.norm(y_at_T["lim"]))
+    tau_c = 1e-9
+    pc = ch.make_params("lim", False, 200 * tau_c, tau_c, wl["tol"], wl["mmax"])
+    yc = {}
+    for name, G in (("mixed", Gm), ("fp64", Gd)):
         y.copy_(y0)
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st64 = ch.ch_integrate(Gd.h, prm[s], y)
+        ch.ch_integrate(G.h, pc, y)
         e1.record(stream); e1.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        mixed_vs_fp64[s] = {"fp64_ms_to_T": ms64, "mixed_ms_to_T": ttt[s]["ms"], "speedup": ms64 / ttt[s]["ms"],
-                            "rel_err_at_T_vs_fp64": float(torch.linalg.norm(y_at_T[s] - y) / torch.linalg.norm(y)),
-                            "fp64_steps": st64["steps"], "mixed_steps": ttt[s]["steps"],
-                            "mixed_mass_drift": float(abs(y_at_T[s].mean() - y0.mean()))}
+        yc[name] = (y.clone(), e0.elapsed_time(e1))
+    mixed_vs_fp64["lim"] = {
+        "mixed_adaptive_ms_to_T": lim_m_ms, "fp64_adaptive_ms_to_T": ttt["lim"]["ms"],
+        "mixed_adaptive_steps": stm["steps"], "fp64_adaptive_steps": ttt["lim"]["steps"],
+        "adaptive_runs_rel_diff_at_T": lim_adapt_diff,
+        "same_200_steps_tau_1e-9": {"mixed_ms": yc["mixed"][1], "fp64_ms": yc["fp64"][1],
+                                    "rel_err": float(torch.linalg.norm(yc["mixed"][0] - yc["fp64"][0])
+                                                     / torch.linalg.norm(yc["fp64"][0]))}}
 
     # ---- end to end through the C ABI with host buffers (one step) ---------------------------
     y_host = torch.from_numpy(y0_host.copy()).pin_memory()
@@ -449,18 +479,22 @@ def main():
     # FP64 LIM kernels (FP64-issue bound) are timed the same way against the measured FP64 peak.
     fp64_peak = ch.ch_probe_fp64_peak(stream)
     live = {}
-    for cls, scheme, G in (("arnoldi", "ee2", Gm), ("lim2", "lim", Gm), ("lim2", "lim", Gd), ("resid1", "lim", Gd)):
-        key = cls if G is Gm else cls + "_fp64"
+    if arn_n > 0 and arn_ms > 0:
+        live["arnoldi"] = {"launches": arn_n, "avg_us": 1e3 * arn_ms / arn_n, "gbs": arn_by / (arn_ms * 1e-3) / 1e9,
+                           "tflops": arn_fl / (arn_ms * 1e-3) / 1e12, "bytes_per_launch": arn_by / arn_n,
+                           "flops_per_launch": arn_fl / arn_n, "total_ms": arn_ms,
+                           "where": "every launch of the timed steps"}
+    for cls in ("lim2", "resid1"):
         y.copy_(y0)
-        ch.ch_timing_start(G.h, cls)
-        ch.ch_integrate(G.h, ch.make_params(scheme, True, wl["T"] / 20, wl["tau0"], wl["tol"], wl["mmax"]), y)
-        ms, nt, _ = ch.ch_timing_read(G.h)
-        fl, by = ch.ch_timing_work(G.h)
-        ch.ch_timing_start(G.h, None)
+        ch.ch_timing_start(Gd.h, cls)
+        ch.ch_integrate(Gd.h, ch.make_params("lim", True, wl["T"] / 20, wl["tau0"], wl["tol"], wl["mmax"]), y)
+        ms, nt, _ = ch.ch_timing_read(Gd.h)
+        fl, by = ch.ch_timing_work(Gd.h)
+        ch.ch_timing_start(Gd.h, None)
         if nt > 0 and ms > 0:
-            live[key] = {"launches": nt, "avg_us": 1e3 * ms / nt, "gbs": by / (ms * 1e-3) / 1e9,
-                         "tflops": fl / (ms * 1e-3) / 1e12, "bytes_per_launch": by / nt,
-                         "flops_per_launch": fl / nt, "launches_in_timed_step": counts.get(cls, 0) // max(1, args.steps)}
+            live[cls + "_fp64"] = {"launches": nt, "avg_us": 1e3 * ms / nt, "gbs": by / (ms * 1e-3) / 1e9,
+                                   "tflops": fl / (ms * 1e-3) / 1e12, "bytes_per_launch": by / nt,
+                                   "flops_per_launch": fl / nt, "where": "LIM over t in [0, T/20]"}
     roof = None
     if "arnoldi" in live:
         kl = live["arnoldi"]
@@ -469,10 +503,10 @@ def main():
                 "frac": kl["gbs"] / HBM_GBS,
                 "traffic": None if ratio is None else ratio * kl["bytes_per_launch"],
                 "peak_source": f"{HBM_SOURCE} (MEASURED_PEAKS.json hbm_gbs)" if HBM_SOURCE == "measured" else "fallback",
-                "measured": f"{kl['launches']} launches timed live over t in [0, T/20]",
+                "measured": f"{kl['launches']} launches of the timed steps, CUDA events on the grid's stream",
                 "avg_launch_us": kl["avg_us"], "algorithmic_bytes_per_launch": kl["bytes_per_launch"],
                 "algorithmic_flops_per_launch": kl["flops_per_launch"],
-                "est_share_of_step": kl["avg_us"] * 1e-3 * kl["launches_in_timed_step"] / (total_ms / args.steps)}
+                "share_of_step": kl["total_ms"] / total_ms}
     fp64_kernels = {c: {**live[c], "frac_of_measured_fp64": live[c]["tflops"] / fp64_peak}
                     for c in ("lim2_fp64", "resid1_fp64") if c in live}
     # the dominant kernel in isolation at a fixed Krylov dimension (j = 10): 20 back-to-back
@@ -507,9 +541,9 @@ def main():
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "ee2 f32/f64 mixed, lim f64", "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, wl), "global_batch": world, "grid_points": N,
-                       "step": "EE2 to T, then LIM to T, both mixed precision, from the same state",
+                       "step": "EE2 (mixed precision) to T, then LIM (FP64) to T, from the same state",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed (256 MiB write) before every timed step; every vector of the workload exceeds L2"},
             "time_to_T": ttt, "mixed_vs_fp64": mixed_vs_fp64, "e2e": e2e, "gpu_launches": launches,

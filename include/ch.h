@@ -251,7 +251,8 @@ ch_status ch_timing_start(ch_grid *g, int kernel_class);
 
 /* Synchronise and report: total event time (ms) and number of timed launches of the timed
  * class, and per-class launch counts since ch_timing_start (counts may be NULL, else an
- * array of CH_K_COUNT entries).                                                          */
+ * array of CH_K_COUNT entries).  Arnoldi iterations queued after their Krylov run ended
+ * return at once; for CH_K_ARNOLDI those launches count neither time nor work.            */
 ch_status ch_timing_read(ch_grid *g, double *total_ms, int64_t *timed_launches,
                          int64_t *counts);
 

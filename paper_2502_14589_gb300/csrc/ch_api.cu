@@ -76,12 +76,14 @@ struct ch_grid {
     std::map<std::tuple<int, const void *, int, int, int>, IterGraph> graphs;
     int use_graphs;
     int fused_arnoldi;            // 1: one cooperative launch per Arnoldi iteration
+    int g64;                      // FP64 grids: Gram-corrected iteration (j <= 31) instead of the
+                                  // sequential passes (grids of at most kG64MaxPoints points)
     int arn_blocks;               // its grid
     double *mfb[3];               // variable-mobility grids: face mobilities (FP64)
     float *mffb[3];               // and their FP32 copies (mixed grids)
     int var_mobility;             // 1: created with room for a variable mobility
-    float2 *gpart;                // mixed grids: reduction scratch of the Gram-corrected iteration
-    double *gram;                 // mixed grids: Gram matrix of the Krylov basis
+    float2 *gpart;                // reduction scratch of the Gram-corrected iterations (8-byte slots)
+    double *gram;                 // Gram matrix of the Krylov basis (Gram-corrected iterations)
     // device workspace
     double *D, *G, *t, *q;        // per-step coefficients and stage scratch
     double *F[2];                 // rhs buffers; F[cur] is basis column 0 of a Krylov run
@@ -219,6 +221,7 @@ static void rhs(ch_grid *g, const double *y, double *out, int eyre, int mode,
 // columns are never combined.  Eight per launch halves the phi launches of a run to m_max
 // = 30 against four, for at most four more speculative iterations when a run stops early.
 constexpr int kPhiBlock = 8;
+constexpr int64_t kG64MaxPoints = (int64_t)1 << 21;
 
 // Krylov dimensions per projected-phi launch for this grid.  Speculative iterations cost
 // an Arnoldi iteration each (about 1 us per 1e4 points: 3-4 ms at 512^3), a phi launch tens
@@ -240,6 +243,14 @@ static void queue_block(ch_grid *g, const Launch &L, VT *slot0, VT *V, const VT 
                 if (j <= ch::kGsMaxJ) {
                     ch::launch_arnoldi_gmgs(L, g->arn_blocks, g->g, slot0, V, g->ldv, Dm, t, g->H, ldh, j,
                                             g->gpart, g->gram, g->mmax_cap + 1);
+                    if (mmax > 63) ch::launch_phi(L, g->H, ldh, j, mmax, g->u, g->phi_scratch);
+                    continue;
+                }
+            }
+            if constexpr (sizeof(VT) == 8) {
+                if (g->g64 && j <= ch::kGsMaxJ) {
+                    ch::launch_arnoldi_g64(L, g->arn_blocks, g->g, slot0, V, g->ldv, Dm, t, g->H, ldh, j,
+                                           (double *)g->gpart, g->gram, g->mmax_cap + 1);
                     if (mmax > 63) ch::launch_phi(L, g->H, ldh, j, mmax, g->u, g->phi_scratch);
                     continue;
                 }
@@ -546,10 +557,14 @@ static ch_status lim_step_impl(ch_grid *g, const double *yn, double tau, double 
 
 void ch::Timing::harvest() {
     if (used == 0) return;
-    cudaEventSynchronize(ev[used - 1]);
-    for (size_t k = 0; k + 1 < used; k += 2) {
+    cudaEventSynchronize(ev[2 * used - 1]);
+    for (size_t k = 0; k < used; ++k) {
+        if (cls == CH_K_ARNOLDI && active && active[k] == 0) continue;    // returned at once
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess) total_ms += ms;
+        if (cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) total_ms += ms;
+        ++timed;
+        flops += wflops[k];
+        bytes += wbytes[k];
     }
     used = 0;
 }
@@ -564,8 +579,12 @@ ch_status ch_timing_start(ch_grid *g, int kernel_class) {
     CUDA_TRY(cudaStreamSynchronize(g->stream));
     g->timing.harvest();
     if (kernel_class >= 0 && g->timing.ev.empty()) {
-        g->timing.ev.resize(2 * 4096);
+        const size_t slots = 4096;
+        g->timing.ev.resize(2 * slots);
         for (auto &e : g->timing.ev) CUDA_TRY(cudaEventCreate(&e));
+        g->timing.wflops.assign(slots, 0.0);
+        g->timing.wbytes.assign(slots, 0.0);
+        CUDA_TRY(cudaMallocHost((void **)&g->timing.active, slots * sizeof(int)));
     }
     g->timing.cls = kernel_class;
     g->timing.used = 0;
@@ -643,6 +662,9 @@ ch_status ch_bench_kernel(ch_grid *g, int kernel_class, int reps, double *avg_us
             const int j = std::min(10, g->mmax_cap);
             if (mixed) ch::launch_arnoldi_gmgs(Lc, g->arn_blocks, g->g, g->Wf[0], g->Vf, g->ldv, g->Df, g->tf,
                                                g->H, g->mmax_cap, j, g->gpart, g->gram, g->mmax_cap + 1);
+            else if (g->g64 && j <= ch::kGsMaxJ)
+                ch::launch_arnoldi_g64(Lc, g->arn_blocks, g->g, g->F[0], g->V, g->ldv, g->D, g->t, g->H, g->mmax_cap, j,
+                                       (double *)g->gpart, g->gram, g->mmax_cap + 1);
             else ch::launch_arnoldi<double>(Lc, g->arn_blocks, g->g, g->F[0], g->V, g->ldv, g->D, g->t, g->H, g->mmax_cap, j);
             bytes = mixed ? (6.0 + 2.0 * j) * vb * N : (5.0 + j) * vb * N;
             flops = mixed ? ((1 + 3.0 * d) + (1 + 3.0 * d) + 6.0 * j + 2.0) * N
@@ -774,6 +796,11 @@ ch_status ch_create_grid_ex(int dim, const int64_t n[3], double eps, int precisi
         g->use_graphs = !(env && env[0] == '1');
         env = getenv("CH_NO_FUSED_ARNOLDI");
         g->fused_arnoldi = !(env && env[0] == '1');
+        // FP64 sequential passes are bound by their j + 2 grid synchronisations on grids up to
+        // about 2M points (a pass of 2 FMAs per point takes less than a barrier's few us);
+        // above that they are bound by FP64 issue or HBM and the Gram form's extra FMAs lose.
+        env = getenv("CH_ARNOLDI_MGS");
+        g->g64 = precision == CH_FP64 && N <= kG64MaxPoints && !(env && env[0] == '1');
     }
 
     auto cleanup_fail = [&](ch_status st, const char *what, cudaError_t e) {
@@ -819,6 +846,8 @@ ch_status ch_create_grid_ex(int dim, const int64_t n[3], double eps, int precisi
             e = cudaMalloc((void **)a.p, a.bytes);
             if (e != cudaSuccess) { cudaGetLastError(); return cleanup_fail(CH_ENOMEM, "cudaMalloc of FP32 basis", e); }
         }
+    }
+    if (precision == CH_MIXED || g->g64) {
         e = cudaMalloc((void **)&g->gpart, sizeof(float2) * 3 * (ch::kGsMaxJ + 1) * (size_t)std::max(g->arn_blocks, 1));
         if (e == cudaSuccess)
             e = cudaMalloc((void **)&g->gram, sizeof(double) * (size_t)(mmax_capacity + 1) * (mmax_capacity + 1));
@@ -872,6 +901,7 @@ ch_status ch_destroy_grid(ch_grid *g) {
     if (g->ev[0]) cudaEventDestroy(g->ev[0]);
     if (g->ev[1]) cudaEventDestroy(g->ev[1]);
     for (auto &e : g->timing.ev) if (e) cudaEventDestroy(e);
+    if (g->timing.active) cudaFreeHost(g->timing.active);
     for (auto &kv : g->graphs) if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;

@@ -188,14 +188,20 @@ __device__ __forceinline__ void block_minmax(double &mn, double &mx) {
 // ---------------------------------------------------------------------------------------
 // Per-class launch counts, and optional CUDA-event timing of every launch of one class
 // (events recorded on the grid's stream right before and after each such launch).
+// Arnoldi iterations are queued ahead of the host's convergence check, so a launch may find
+// its Krylov run already ended and return at once: for that class the control block's
+// `active` flag is copied to pinned memory before each timed launch, and launches that found
+// it 0 count neither time nor work.
 struct Timing {
     int cls = -1;                       // class being timed, -1 = none
-    std::vector<cudaEvent_t> ev;        // 2 events per timed launch
-    size_t used = 0;                    // events in use
+    std::vector<cudaEvent_t> ev;        // 2 events per timed launch (slot)
+    std::vector<double> wflops, wbytes; // algorithmic work of each slot
+    int *active = nullptr;              // pinned: `active` at each slot's launch (Arnoldi class)
+    size_t used = 0;                    // slots in use
     double total_ms = 0.0;
-    int64_t timed = 0;
+    int64_t timed = 0;                  // timed launches that did work
     int64_t counts[CH_K_COUNT] = {0};
-    double flops = 0.0, bytes = 0.0;    // algorithmic work of the timed launches
+    double flops = 0.0, bytes = 0.0;    // algorithmic work of the timed launches that did work
     void harvest();                     // defined in ch_api.cu
 };
 
@@ -219,9 +225,14 @@ struct LaunchScope {
         if (!L.timing) return;
         ++L.timing->counts[c];
         if (L.timing->cls == c) {
-            if (L.timing->used + 2 > L.timing->ev.size()) L.timing->harvest();
-            if (L.timing->used + 2 <= L.timing->ev.size()) {
-                cudaEventRecord(L.timing->ev[L.timing->used], L.stream);
+            Timing &T = *L.timing;
+            if (2 * (T.used + 1) > T.ev.size()) T.harvest();
+            if (2 * (T.used + 1) <= T.ev.size()) {
+                T.wflops[T.used] = T.wbytes[T.used] = 0.0;
+                if (c == CH_K_ARNOLDI && T.active)
+                    cudaMemcpyAsync(&T.active[T.used], &L.ctrl->active, sizeof(int), cudaMemcpyDeviceToHost,
+                                    L.stream);
+                cudaEventRecord(T.ev[2 * T.used], L.stream);
                 timed = true;
             }
         }
@@ -230,14 +241,13 @@ struct LaunchScope {
     // bytes the method must move), accumulated when the launch is timed.
     void work(double flops, double bytes) const {
         if (!timed) return;
-        L.timing->flops += flops;
-        L.timing->bytes += bytes;
+        L.timing->wflops[L.timing->used] = flops;
+        L.timing->wbytes[L.timing->used] = bytes;
     }
     ~LaunchScope() {
         if (!timed) return;
-        cudaEventRecord(L.timing->ev[L.timing->used + 1], L.stream);
-        L.timing->used += 2;
-        ++L.timing->timed;
+        cudaEventRecord(L.timing->ev[2 * L.timing->used + 1], L.stream);
+        ++L.timing->used;
     }
 };
 
@@ -268,6 +278,11 @@ constexpr int kGsMaxJ = 31;
 void launch_arnoldi_gmgs(const Launch &L, int blocks, const Geom &g, float *slot0, float *V,
                          int64_t ldv, const float *D, float *t, double *H, int ldh, int j,
                          float2 *gpart, double *gram, int ldg);
+// FP64-basis Arnoldi iteration j <= kGsMaxJ with the Gram-corrected coefficients (three grid
+// synchronisations); gpart: 3 x (kGsMaxJ + 1) x blocks doubles, gram as above.
+void launch_arnoldi_g64(const Launch &L, int blocks, const Geom &g, double *slot0, double *V,
+                        int64_t ldv, const double *D, double *t, double *H, int ldh, int j,
+                        double *gpart, double *gram, int ldg);
 int arnoldi_setup();   // cudaError_t of setting the kernels' shared-memory limits
 void launch_combine32(const Launch &L, int64_t N, const double *y0, const float *v0,
                       const float *V, int64_t ldv, float *d, double *ynext);

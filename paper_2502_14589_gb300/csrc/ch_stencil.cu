@@ -1045,6 +1045,217 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Arnoldi iteration j for an FP64 basis with the Gram-corrected coefficients (the identity
+// h_kj = c_k - sum_{i<k} G_ki h_ij of k_arnoldi_gmgs, in FP64 throughout):
+//   stage 1, stage 2 (w = A_hat v_j into the W_{j+1} slot)       | barrier after stage 1
+//   round A: c_k = v_k . w (k = 1..j), G_ji = v_j . v_i (i < j)   | grid reduction
+//   forward substitution for h_kj (warp 0 of every block, identical)
+//   round B: w' = w - sum_k h_kj v_k and ||w'||^2                 | grid reduction
+// Three grid synchronisations per iteration instead of j + 2, for 2j + 1 more FMAs per point
+// than the sequential passes: the form for grids whose passes are bound by synchronisation
+// rather than by FP64 issue or HBM (up to kG64MaxPoints points).  FP64 block and grid sums
+// in a fixed order: deterministic.  gpart holds 2 (kGsMaxJ + 1) G partials, gram the Gram
+// rows of the run (row k for vector k + 1, ldg = row stride).
+// ---------------------------------------------------------------------------------------
+constexpr int kG64Vals = 8;                  // values per block reduction (4 columns x 2)
+
+// Block sums of nv <= 8 per-thread doubles acc[q] (1024 threads), in out[q] for all threads.
+__device__ __forceinline__ void g64_block_sums(const double (&acc)[kG64Vals], int nv, double *red,
+                                               double *out) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < kG64Vals; ++q) red[q * kArnThreads + tid] = acc[q];
+    __syncthreads();
+    const int wq = tid >> 5, lane = tid & 31;
+    if (wq < nv) {      // warp q adds value q: 32 per lane in pairwise groups of 8, then shuffles
+        const double *p = red + wq * kArnThreads + lane;
+        double c[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            double v[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[m] = p[32 * (8 * h + m)];
+            c[h] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        }
+        double a = (c[0] + c[1]) + (c[2] + c[3]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) out[wq] = a;
+    }
+    __syncthreads();
+}
+
+// Sum of the G per-block partials part[0..G) by one warp (any warp of the block), pairwise
+// in a fixed order; valid in its lane 0 and identical in every block.
+__device__ __forceinline__ double g64_grid_sum(const double *part) {
+    const unsigned G = gridDim.x, lane = threadIdx.x & 31u;
+    double v[5];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) v[s] = (lane + 32u * s < G) ? __ldcg(&part[lane + 32u * s]) : 0.0;
+    double a = ((v[0] + v[1]) + (v[2] + v[3])) + v[4];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    return a;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kArnThreads, 1)
+k_arnoldi_g64(Geom g, double *__restrict__ slot0, double *__restrict__ V, int64_t ldv,
+              const double *__restrict__ D, double *__restrict__ t, double *H, int ldh, int j,
+              double *gpart, double *gram, int ldg, Ctrl *ctrl) {
+    if (!ctrl->active) return;                  // same value in every block
+    extern __shared__ __align__(16) unsigned char dyn[];
+    double *red = reinterpret_cast<double *>(dyn);            // kG64Vals x 1024
+    __shared__ double bout[kG64Vals];
+    __shared__ double gams[kGsMaxJ + 1];
+    __shared__ double cs[kGsMaxJ + 1];
+    __shared__ double gs[kGsMaxJ][kGsMaxJ + 1];    // G_ki (k > i), 0-based
+    __shared__ double as[kGsMaxJ];
+    auto W = [&](int c) -> double * { return c == 1 ? slot0 : V + (int64_t)(c - 2) * ldv; };
+    GridBarrier gb(&ctrl->bar, &ctrl->status);
+    const unsigned N = (unsigned)g.N;
+    const unsigned G = gridDim.x;
+    double *w = W(j + 1);
+    double *pA = gpart, *pB = gpart + (size_t)2 * (kGsMaxJ + 1) * G;
+    for (int e = threadIdx.x; e < j; e += blockDim.x) gams[e] = ctrl->gam[e];
+    for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
+        const int k = e / j, i = e % j;
+        gs[k][i] = (i < k && k < j - 1) ? gram[(size_t)k * ldg + i] : 0.0;
+    }
+    // ---- stage 1: t = D (.) x - sum_a kap_a (x_{+a} + x_{-a})
+    {
+        const double *x = W(j);
+        GRID_LOOP2(N, {
+            t[i] = stage1_at<DIM, double>(g, x, D, i, g.kap[0], g.kap[1], g.kap[2]);
+        })
+    }
+    gb.sync();
+    // ---- stage 2: w = gam_j (sigma t - sum_a s_a (t_{+a} + t_{-a}))
+    {
+        const double gam = gams[j - 1];
+        const double c0 = gam * g.sigma, c1 = gam * g.s[0], c2 = gam * g.s[1], c3 = gam * g.s[2];
+        GRID_LOOP2(N, {
+            w[i] = stage2_at<DIM, double>(g, t, i, c0, c1, c2, c3, gam);
+        })
+    }
+    // ---- round A: c_k = W_k . w and W_k . W_j, four columns per sweep over this thread's points
+    const double *xj = W(j);
+    for (int k0 = 1; k0 <= j; k0 += 4) {
+        const int nk = min(4, j - k0 + 1);
+        double acc[kG64Vals];
+#pragma unroll
+        for (int q = 0; q < kG64Vals; ++q) acc[q] = 0.0;
+        const double *v0 = W(k0), *v1 = nk > 1 ? W(k0 + 1) : v0, *v2 = nk > 2 ? W(k0 + 2) : v0,
+                     *v3 = nk > 3 ? W(k0 + 3) : v0;
+        GRID_LOOP(i, N) {
+            const double wv = w[i], xv = xj[i];
+            const double a0 = v0[i], a1 = v1[i], a2 = v2[i], a3 = v3[i];
+            acc[0] = fma(wv, a0, acc[0]); acc[4] = fma(xv, a0, acc[4]);
+            acc[1] = fma(wv, a1, acc[1]); acc[5] = fma(xv, a1, acc[5]);
+            acc[2] = fma(wv, a2, acc[2]); acc[6] = fma(xv, a2, acc[6]);
+            acc[3] = fma(wv, a3, acc[3]); acc[7] = fma(xv, a3, acc[7]);
+        }
+        g64_block_sums(acc, kG64Vals, red, bout);
+        if (threadIdx.x == 0)
+            for (int u = 0; u < nk; ++u) {
+                pA[(size_t)(k0 - 1 + u) * G + blockIdx.x] = bout[u];
+                if (k0 + u < j) pA[(size_t)(kGsMaxJ + 1 + k0 - 1 + u) * G + blockIdx.x] = bout[4 + u];
+            }
+    }
+    gb.sync();
+    {   // slot k-1: W_k . w;  slot 32 + i - 1: W_i . W_j  (warp v sums value v over the blocks)
+        const int wq = threadIdx.x >> 5;
+        for (int v = wq; v < 2 * j - 1; v += 32) {
+            const bool isc = v < j;
+            const int k = isc ? v : v - j;
+            const double sum = g64_grid_sum(pA + (size_t)(isc ? k : kGsMaxJ + 1 + k) * G);
+            if ((threadIdx.x & 31) == 0) {
+                if (isc) {
+                    cs[k] = gams[k] * sum;                                    // c_k = v_k . w
+                } else {
+                    const double gji = gams[j - 1] * gams[k] * sum;           // G_jk = v_j . v_k
+                    gs[j - 1][k] = gji;
+                    if (blockIdx.x == 0) gram[(size_t)(j - 1) * ldg + k] = gji;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // ---- forward substitution h_k = c_k - sum_{i<k} G_ki h_i, sequential (lane k-1 of warp 0)
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        double corr = 0.0;
+        for (int i = 0; i < j; ++i) {
+            const double hi = __shfl_sync(0xffffffffu, (l < j ? cs[l] : 0.0) - corr, i);
+            if (l > i && l < j) corr = fma(gs[l][i], hi, corr);
+        }
+        if (l < j) {
+            const double h = cs[l] - corr;
+            as[l] = h * gams[l];
+            if (blockIdx.x == 0) H[l * ldh + (j - 1)] = h;
+        }
+    }
+    __syncthreads();
+    // ---- round B: w' = w - sum_k h_kj v_k (eight columns per batch) and ||w'||^2
+    {
+        double nrm = 0.0;
+        GRID_LOOP(i, N) {
+            double x = w[i];
+            for (int k0 = 1; k0 <= j; k0 += 8) {
+                double v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = k0 + u <= j ? W(k0 + u)[i] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (k0 + u <= j) x = fma(-as[k0 + u - 1], v[u], x);
+            }
+            w[i] = x;
+            nrm = fma(x, x, nrm);
+        }
+        double acc[kG64Vals] = {nrm, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        g64_block_sums(acc, 1, red, bout);
+        if (threadIdx.x == 0) pB[blockIdx.x] = bout[0];
+    }
+    gb.sync();
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const double nrm2 = g64_grid_sum(pB);
+        if (threadIdx.x == 0) {
+            const double hn = sqrt(nrm2);                         // h_{j+1,j} (Fig. 2)
+            ctrl->hnext2 = nrm2;
+            H[j * ldh + (j - 1)] = hn;
+            ctrl->gam[j] = 1.0 / hn;
+        }
+    }
+}
+
+constexpr int kG64SmemBytes = kG64Vals * kArnThreads * (int)sizeof(double);
+
+void launch_arnoldi_g64(const Launch &L, int blocks, const Geom &g, double *slot0, double *V,
+                        int64_t ldv, const double *D, double *t, double *H, int ldh, int j,
+                        double *gpart, double *gram, int ldg) {
+    LaunchScope scope(L, CH_K_ARNOLDI);
+    {   // algorithmic work of the iteration as the sequential passes count it (the Gram form
+        // does 2j + 1 more FMAs per point, which are not counted as work)
+        const double N = (double)g.N, d = g.dim;
+        scope.work(((1.0 + 3.0 * d) + (3.0 + 3.0 * d) + 4.0 * j) * N, (5.0 + j) * 8.0 * N);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks, 1, 1);
+    cfg.blockDim = dim3(kArnThreads, 1, 1);
+    cfg.dynamicSmemBytes = kG64SmemBytes;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (g.dim == 3)
+        cudaLaunchKernelEx(&cfg, k_arnoldi_g64<3>, g, slot0, V, ldv, D, t, H, ldh, j, gpart, gram, ldg, L.ctrl);
+    else
+        cudaLaunchKernelEx(&cfg, k_arnoldi_g64<2>, g, slot0, V, ldv, D, t, H, ldh, j, gpart, gram, ldg, L.ctrl);
+}
+
 void launch_arnoldi_gmgs(const Launch &L, int blocks, const Geom &g, float *slot0, float *V,
                          int64_t ldv, const float *D, float *t, double *H, int ldh, int j,
                          float2 *gpart, double *gram, int ldg) {
@@ -1131,6 +1342,11 @@ int arnoldi_setup() {
     const void *gfns[] = {(const void *)k_arnoldi_gmgs<2>, (const void *)k_arnoldi_gmgs<3>};
     for (const void *f : gfns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kGsSmemBytes);
+        if (e != cudaSuccess) return (int)e;
+    }
+    const void *g64fns[] = {(const void *)k_arnoldi_g64<2>, (const void *)k_arnoldi_g64<3>};
+    for (const void *f : g64fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kG64SmemBytes);
         if (e != cudaSuccess) return (int)e;
     }
     return 0;

@@ -364,7 +364,8 @@ def test_full_size_first_steps(ch, oracle, c1):
 
 
 @pytest.mark.parametrize("env", [{"CH_NO_FUSED_ARNOLDI": "1"}, {"CH_NO_GRAPHS": "1"},
-                                 {"CH_NO_FUSED_ARNOLDI": "1", "CH_NO_GRAPHS": "1"}])
+                                 {"CH_NO_FUSED_ARNOLDI": "1", "CH_NO_GRAPHS": "1"},
+                                 {"CH_ARNOLDI_MGS": "1"}])
 @pytest.mark.parametrize("dim,n,tau", [(2, (64, 64), 1e-6), (3, (10, 9, 11), 3e-5)])
 def test_launch_variants_match_oracle(ch, oracle, monkeypatch, env, dim, n, tau):
     """Arnoldi iterations as separate kernels, and without CUDA graphs (both read when a grid
@@ -470,3 +471,28 @@ def test_ee2_mmax100_constant_steps_with_restarts(ch, oracle):
     np.testing.assert_array_equal(rec["jexit"], reco["jexit"])
     np.testing.assert_array_equal(rec["restarts"], reco["restarts"])
     assert rel(yg, yo) < 1e-10
+
+
+@pytest.mark.parametrize("dim,n,tau", [(2, (1024, 1024), 3e-8), (2, (256, 192), 2e-6), (3, (64, 64, 64), 1e-6)])
+def test_fp64_gram_iteration_against_sequential_passes(ch, oracle, monkeypatch, dim, n, tau):
+    """FP64 grids of up to 2M points compute the coefficients of Fig. 2's modified
+    Gram-Schmidt through the Gram identity h_kj = c_k - sum_{i<k} G_ki h_ij (three grid
+    synchronisations per iteration); larger ones, or CH_ARNOLDI_MGS=1, run the passes one
+    by one.  Both forms give the oracle's Krylov run: the same step, the same exit
+    dimension and y within 1e-12."""
+    eps, tol_phi = 0.01 if dim == 2 else 0.02, 1e-8
+    y = inputs.initial_state(n, 6, -0.05, 0.05)
+    out = {}
+    for mgs in ("0", "1"):
+        monkeypatch.setenv("CH_ARNOLDI_MGS", mgs)
+        with ch.Grid(dim, n, eps, mmax_capacity=30) as G:
+            yn = torch.empty(G.N, dtype=torch.float64, device="cuda")
+            tu, st = ch.ch_phi_krylov(G.h, dev(y), tau, tol_phi, 30, 0, yn)
+            out[mgs] = (tu, st["matvecs"], host(yn))
+    rc, yo, to, jo, sto = oracle.ee_step(oracle.Grid(dim, n, eps), y, tau, tol_phi_fixed=tol_phi, mmax=30,
+                                         linear_restart=False)
+    assert rc == 0
+    for mgs, (tu, mv, yg) in out.items():
+        assert tu == pytest.approx(to, rel=1e-12, abs=0), mgs
+        assert mv == sto["matvecs"], mgs
+        assert rel(yg, yo) < 1e-12, mgs
