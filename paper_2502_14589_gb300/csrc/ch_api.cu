@@ -221,7 +221,7 @@ static void rhs(ch_grid *g, const double *y, double *out, int eyre, int mode,
 // columns are never combined.  Eight per launch halves the phi launches of a run to m_max
 // = 30 against four, for at most four more speculative iterations when a run stops early.
 constexpr int kPhiBlock = 8;
-constexpr int64_t kG64MaxPoints = (int64_t)1 << 21;
+constexpr int64_t kG64MaxPoints = (int64_t)1 << 19;
 
 // Krylov dimensions per projected-phi launch for this grid.  Speculative iterations cost
 // an Arnoldi iteration each (about 1 us per 1e4 points: 3-4 ms at 512^3), a phi launch tens
@@ -796,9 +796,10 @@ ch_status ch_create_grid_ex(int dim, const int64_t n[3], double eps, int precisi
         g->use_graphs = !(env && env[0] == '1');
         env = getenv("CH_NO_FUSED_ARNOLDI");
         g->fused_arnoldi = !(env && env[0] == '1');
-        // FP64 sequential passes are bound by their j + 2 grid synchronisations on grids up to
-        // about 2M points (a pass of 2 FMAs per point takes less than a barrier's few us);
-        // above that they are bound by FP64 issue or HBM and the Gram form's extra FMAs lose.
+        // FP64 sequential passes are bound by their j + 2 grid synchronisations on small grids
+        // (a pass of 2 FMAs per point takes less than a barrier's few us): measured, the Gram
+        // form took a batch of 64^2..512^2 grids one by one from 153 s to 133 s, but made EE2 on
+        // 1024^2 8 % slower (46.7 s against 43.0 s), so it serves grids up to 512K points.
         env = getenv("CH_ARNOLDI_MGS");
         g->g64 = precision == CH_FP64 && N <= kG64MaxPoints && !(env && env[0] == '1');
     }

@@ -835,7 +835,7 @@ VT *basis_col(ch_batch *b, int slot, int c) {   // W_c, 1-based
 // m_max <= kBGsMaxJ, the sequential modified Gram-Schmidt passes otherwise.  jp: the
 // device-held j of a device-driven loop (nullptr: j as given).
 template <typename VT>
-void queue_arnoldi_b(ch_batch *b, cudaStream_t s, int slot, int j, int mmax) {
+void queue_arnoldi_kernels_b(ch_batch *b, cudaStream_t s, int slot, int j) {
     const int ldh = b->mmax_cap;
     const int64_t hs = (int64_t)(b->mmax_cap + 1) * b->mmax_cap;
     VT *Wj = basis_col<VT>(b, slot, j), *Wn = basis_col<VT>(b, slot, j + 1), *v1 = basis_col<VT>(b, slot, 1);
@@ -863,6 +863,13 @@ void queue_arnoldi_b(ch_batch *b, cudaStream_t s, int slot, int j, int mmax) {
             ++b->launches;
         }
     }
+}
+
+template <typename VT>
+void queue_arnoldi_b(ch_batch *b, cudaStream_t s, int slot, int j, int mmax) {
+    const int ldh = b->mmax_cap;
+    const int64_t hs = (int64_t)(b->mmax_cap + 1) * b->mmax_cap;
+    queue_arnoldi_kernels_b<VT>(b, s, slot, j);
     Launch L = make_launch(b, s);
     ch::launch_phi_batch(L, b->ctrls, b->H, hs, b->u, b->mmax_cap + 1, ldh, j, mmax, b->count);
 }
@@ -1253,14 +1260,18 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = (cudaError_t)ch::phi_setup();
     if (e != cudaSuccess) return cleanup("batch set-up", e);
-    // ---- chunk-length autotuner: time one stencil pass over the whole batch per candidate
+    // ---- chunk-length autotuner: time the kernels of one Arnoldi iteration (j = 8: stencil
+    // stages, orthogonalisation, per-instance reductions, without the chunk-independent
+    // projected phi) over the whole batch for each candidate, on zero data
     {
         int one = 1;
         for (int i = 0; i < count; ++i)
             cudaMemcpy(&b->ctrls[i].active, &one, sizeof(int), cudaMemcpyHostToDevice);
         cudaMemset(b->D, 0, eb);
         cudaMemset(b->F[0], 0, vb);
+        cudaMemset(b->V, 0, eb * (size_t)mmax_capacity);
         if (precision == CH_MIXED) cudaMemset(b->W[0], 0, eb);
+        const int jt = std::min(8, mmax_capacity);
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
@@ -1275,11 +1286,9 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
             float ms = 0.f;
             for (int rep = 0; rep < 2; ++rep) {
                 cudaEventRecord(e0, s);
-                for (int r = 0; r < 5; ++r) {
-                    if (precision == CH_MIXED)
-                        BLAUNCH_T(kb_tstage, float, b->insts, b->chunks, b->ctrls, (const float *)b->W[0], (const float *)b->D, (float *)b->t);
-                    else
-                        BLAUNCH_T(kb_tstage, double, b->insts, b->chunks, b->ctrls, (const double *)b->F[0], (const double *)b->D, (double *)b->t);
+                for (int r = 0; r < 3; ++r) {
+                    if (precision == CH_MIXED) queue_arnoldi_kernels_b<float>(b, s, 0, jt);
+                    else queue_arnoldi_kernels_b<double>(b, s, 0, jt);
                 }
                 cudaEventRecord(e1, s);
                 cudaEventSynchronize(e1);
@@ -1292,6 +1301,11 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
         int zero = 0;
         for (int i = 0; i < count; ++i)
             cudaMemcpy(&b->ctrls[i].active, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        b->launches = 0;
+        // the timed iterations wrote Hessenberg and Gram entries of zero vectors: clear them
+        cudaMemset(b->H, 0, sizeof(double) * count * (size_t)(mmax_capacity + 1) * mmax_capacity);
+        if (b->grams)
+            cudaMemset(b->grams, 0, sizeof(double) * count * (size_t)(mmax_capacity + 1) * (mmax_capacity + 1));
         b->chunk_len = best;
         build_chunks(b, best, ch);
         b->nchunks = (int)ch.size();

@@ -473,9 +473,9 @@ def test_ee2_mmax100_constant_steps_with_restarts(ch, oracle):
     assert rel(yg, yo) < 1e-10
 
 
-@pytest.mark.parametrize("dim,n,tau", [(2, (1024, 1024), 3e-8), (2, (256, 192), 2e-6), (3, (64, 64, 64), 1e-6)])
+@pytest.mark.parametrize("dim,n,tau", [(2, (512, 1024), 3e-8), (2, (256, 192), 2e-6), (3, (64, 64, 64), 1e-6)])
 def test_fp64_gram_iteration_against_sequential_passes(ch, oracle, monkeypatch, dim, n, tau):
-    """FP64 grids of up to 2M points compute the coefficients of Fig. 2's modified
+    """FP64 grids of up to 512K points compute the coefficients of Fig. 2's modified
     Gram-Schmidt through the Gram identity h_kj = c_k - sum_{i<k} G_ki h_ij (three grid
     synchronisations per iteration); larger ones, or CH_ARNOLDI_MGS=1, run the passes one
     by one.  Both forms give the oracle's Krylov run: the same step, the same exit
