@@ -843,66 +843,65 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
         if (4u * q + 2u < N) r.z = col[4u * q + 2u];
         return r;                                   // a partial group has at most 3 points
     };
-    // ---- stage 2: w = gam_j sum_a s_a ((t - t_{+a}) + (t - t_{-a})) = A_hat v_j
-    {
-        const double gam = ctrl->gam[j - 1];
-        const float c0 = (float)(gam * g.sigma), c1 = (float)(gam * g.s[0]), c2 = (float)(gam * g.s[1]),
-                    c3 = (float)(gam * g.s[2]);
+    // ---- stage 2: w = gam_j sum_a s_a ((t - t_{+a}) + (t - t_{-a})) = A_hat v_j, one group of
+    //      four points (zeros past N)
+    const double gam2 = ctrl->gam[j - 1];
+    const float sc0 = (float)(gam2 * g.sigma), sc1 = (float)(gam2 * g.s[0]), sc2 = (float)(gam2 * g.s[1]),
+                sc3 = (float)(gam2 * g.s[2]);
+    auto stage2_group = [&](unsigned q) -> float4 {
         if (rows4) {
-            for (unsigned q = q0, ri = 0; q < NG; q += S, ++ri) {
-                float4 tc, d[3];
-                group_diffs<DIM>(g, t, q, tc, d);
-                float4 r;
-                r.x = c1 * d[0].x; r.y = c1 * d[0].y; r.z = c1 * d[0].z; r.w = c1 * d[0].w;
-                r.x = fmaf(c2, d[1].x, r.x); r.y = fmaf(c2, d[1].y, r.y);
-                r.z = fmaf(c2, d[1].z, r.z); r.w = fmaf(c2, d[1].w, r.w);
-                if (DIM == 3) {
-                    r.x = fmaf(c3, d[2].x, r.x); r.y = fmaf(c3, d[2].y, r.y);
-                    r.z = fmaf(c3, d[2].z, r.z); r.w = fmaf(c3, d[2].w, r.w);
-                }
-                if (res) {
-                    wsm[ri * kArnThreads + threadIdx.x] = r;
-                    xsm[ri * kArnThreads + threadIdx.x] = reinterpret_cast<const float4 *>(W(j))[q];
-                } else {
-                    reinterpret_cast<float4 *>(w)[q] = r;
-                }
+            float4 tc, d[3];
+            group_diffs<DIM>(g, t, q, tc, d);
+            float4 r;
+            r.x = sc1 * d[0].x; r.y = sc1 * d[0].y; r.z = sc1 * d[0].z; r.w = sc1 * d[0].w;
+            r.x = fmaf(sc2, d[1].x, r.x); r.y = fmaf(sc2, d[1].y, r.y);
+            r.z = fmaf(sc2, d[1].z, r.z); r.w = fmaf(sc2, d[1].w, r.w);
+            if (DIM == 3) {
+                r.x = fmaf(sc3, d[2].x, r.x); r.y = fmaf(sc3, d[2].y, r.y);
+                r.z = fmaf(sc3, d[2].z, r.z); r.w = fmaf(sc3, d[2].w, r.w);
             }
-        } else {
-            for (unsigned q = q0, ri = 0; q < NG; q += S, ++ri) {
-                float r[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (unsigned e = 0; e < 4u; ++e)
-                    if (4u * q + e < N) r[e] = stage2_at<DIM, float>(g, t, 4u * q + e, c0, c1, c2, c3, (float)gam);
-                if (res) {
-                    wsm[ri * kArnThreads + threadIdx.x] = make_float4(r[0], r[1], r[2], r[3]);
-                    xsm[ri * kArnThreads + threadIdx.x] = ld4(W(j), q, 4u * q + 3u < N);
-                } else {
-#pragma unroll
-                    for (unsigned e = 0; e < 4u; ++e)
-                        if (4u * q + e < N) w[4u * q + e] = r[e];
-                }
-            }
+            return r;
         }
-    }
-    // ---- round A: one sweep gives c_k = v_k . w (k = 1..j) and the Gram row of the newest
-    //      basis vector, G_ji = v_j . v_i (i < j): each column is read once for both, four
-    //      columns per pass over the points with their 16-byte loads issued together.
-    //      Consecutive sweeps walk the basis in opposite directions, so each starts on the
-    //      columns read last, the likeliest to be still in L2.
+        float r[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (unsigned e = 0; e < 4u; ++e)
+            if (4u * q + e < N) r[e] = stage2_at<DIM, float>(g, t, 4u * q + e, sc0, sc1, sc2, sc3, (float)gam2);
+        return make_float4(r[0], r[1], r[2], r[3]);
+    };
+    auto st4 = [&](float *col, unsigned q, bool full, const float4 &v) {
+        if (full) {
+            reinterpret_cast<float4 *>(col)[q] = v;
+        } else {
+            if (4u * q + 0u < N) col[4u * q + 0u] = v.x;
+            if (4u * q + 1u < N) col[4u * q + 1u] = v.y;
+            if (4u * q + 2u < N) col[4u * q + 2u] = v.z;
+        }
+    };
+    // the four products of a group are summed with plain FP32 FMAs (their rounding, random
+    // over the grid, stays far below the basis rounding after the exact cross-thread sums);
+    // only the running sums are compensated
+    auto dot4 = [](const float4 &a, const float4 &b) {
+        return __fmaf_rn(a.w, b.w, __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x))));
+    };
     const bool down = (j & 1) != 0;
     const float *xj = W(j);
-    {
-        const int ncA = (j + 3) / 4;
+    const int ncA = (j + 3) / 4;
+    // Round A: one sweep gives c_k = v_k . w (k = 1..j) and the Gram row of the newest basis
+    // vector, G_ji = v_j . v_i (i < j): each column is read once for both, four columns per
+    // pass over the points with their 16-byte loads issued together.  Consecutive sweeps
+    // walk the basis in opposite directions, so each starts on the columns read last, the
+    // likeliest to be still in L2.
+    if (res) {
+        // grids of at most 8 points per thread: w and v_j stay in shared memory from stage 2
+        // to the end of the iteration
+        for (unsigned q = q0, ri = 0; q < NG; q += S, ++ri) {
+            wsm[ri * kArnThreads + threadIdx.x] = stage2_group(q);
+            xsm[ri * kArnThreads + threadIdx.x] = ld4(xj, q, 4u * q + 3u < N);
+        }
         for (int cA = 0; cA < ncA; ++cA) {
             const int k0 = 1 + (down ? ncA - 1 - cA : cA) * 4;
             const int nk = min(4, j - k0 + 1);
             DotAcc<float> acc[kGsChunk];                  // [u]: W_k . w, [4 + u]: W_k . W_j
-            // the four products of a group are summed with plain FP32 FMAs (their rounding,
-            // random over the grid, stays far below the basis rounding after the exact
-            // cross-thread sums); only the running per-thread sum is compensated
-            auto dot4 = [](const float4 &a, const float4 &b) {
-                return __fmaf_rn(a.w, b.w, __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x))));
-            };
             auto accum = [&](const float4 (&v)[4], const float4 &wv, const float4 &xv) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
@@ -911,33 +910,142 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
                         if (k0 + u < j) acc[4 + u].add_value(dot4(xv, v[u]));
                     }
             };
-            if (res) {   // both groups of the thread: all eight loads in flight at once
-                const unsigned qa = q0, qb = q0 + S;
-                const bool ha = qa < NG, hb = qb < NG;
-                const bool fa = 4u * qa + 3u < N, fb = 4u * qb + 3u < N;
-                float4 va[4], vb[4];
+            // both groups of the thread: all eight loads in flight at once
+            const unsigned qa = q0, qb = q0 + S;
+            const bool ha = qa < NG, hb = qb < NG;
+            const bool fa = 4u * qa + 3u < N, fb = 4u * qb + 3u < N;
+            float4 va[4], vb[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    va[u] = (ha && u < nk) ? ld4(W(k0 + u), qa, fa) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    vb[u] = (hb && u < nk) ? ld4(W(k0 + u), qb, fb) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                if (ha) accum(va, wsm[threadIdx.x], xsm[threadIdx.x]);
-                if (hb) accum(vb, wsm[kArnThreads + threadIdx.x], xsm[kArnThreads + threadIdx.x]);
-            } else for (unsigned q = q0; q < NG; q += S) {
-                const bool full = 4u * q + 3u < N;
-                const float4 wv = ld4(w, q, full), xv = ld4(xj, q, full);
-                float4 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    v[u] = u < nk ? ld4(W(k0 + u), q, full) : make_float4(0.f, 0.f, 0.f, 0.f);
-                accum(v, wv, xv);
+            for (int u = 0; u < 4; ++u) {
+                va[u] = (ha && u < nk) ? ld4(W(k0 + u), qa, fa) : make_float4(0.f, 0.f, 0.f, 0.f);
+                vb[u] = (hb && u < nk) ? ld4(W(k0 + u), qb, fb) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            if (ha) accum(va, wsm[threadIdx.x], xsm[threadIdx.x]);
+            if (hb) accum(vb, wsm[kArnThreads + threadIdx.x], xsm[kArnThreads + threadIdx.x]);
             gs_block_sums(acc, kGsChunk, red, bout);
             const int u = threadIdx.x & 3;
             if (threadIdx.x < 4 && u < nk)
                 pA[(size_t)(k0 - 1 + u) * G + blockIdx.x] = bout[u];
             else if (threadIdx.x >= 4 && threadIdx.x < 8 && u < nk && k0 + u < j)
                 pA[(size_t)(kGsMaxJ + 1 + k0 - 1 + u) * G + blockIdx.x] = bout[4 + u];
+        }
+    } else {
+        // Larger grids: stage 2 runs here, tile by tile (two groups per thread), and each
+        // tile's w and v_j meet every basis column while still on chip, so w is written once
+        // and neither it nor v_j is read again in this round (v_j serves as column j too).
+        // Per-thread sums cover one tile and one column chunk; they are added across the
+        // warp by a transposing shuffle tree and accumulated in the warp's 64 pair slots in
+        // shared memory (slot k - 1: W_k . w, slot 32 + i - 1: W_i . W_j).
+        float2 *accw = red + (threadIdx.x >> 5) * 64;
+        const unsigned lane = threadIdx.x & 31u;
+        accw[lane] = make_float2(0.f, 0.f);
+        accw[32 + lane] = make_float2(0.f, 0.f);
+        __syncwarp();
+        for (unsigned qa = q0; qa < NG; qa += 2u * S) {
+            const unsigned qb = qa + S;
+            const bool hb = qb < NG;
+            const bool fa = 4u * qa + 3u < N, fb = hb && 4u * qb + 3u < N;
+            {
+                const float4 wa = stage2_group(qa);
+                st4(w, qa, fa, wa);
+                wsm[threadIdx.x] = wa;
+                xsm[threadIdx.x] = ld4(xj, qa, fa);
+                const float4 wb = hb ? stage2_group(qb) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (hb) st4(w, qb, fb, wb);
+                wsm[kArnThreads + threadIdx.x] = wb;
+                xsm[kArnThreads + threadIdx.x] = hb ? ld4(xj, qb, fb) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            for (int cA = 0; cA < ncA; ++cA) {
+                const int k0 = 1 + (down ? ncA - 1 - cA : cA) * 4;
+                const int nk = min(4, j - k0 + 1);
+                float4 va[4], vb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (u < nk && k0 + u < j) {
+                        va[u] = ld4(W(k0 + u), qa, fa);
+                        vb[u] = hb ? ld4(W(k0 + u), qb, fb) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else if (u < nk) {                    // column j is v_j itself
+                        va[u] = xsm[threadIdx.x];
+                        vb[u] = xsm[kArnThreads + threadIdx.x];
+                    } else {
+                        va[u] = vb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+                DotAcc<float> acc[kGsChunk];                  // [u]: W_k . w, [4 + u]: W_k . W_j
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float4 wv = wsm[r * kArnThreads + threadIdx.x], xv = xsm[r * kArnThreads + threadIdx.x];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        acc[u].add_value(dot4(wv, r == 0 ? va[u] : vb[u]));
+                        acc[4 + u].add_value(dot4(xv, r == 0 ? va[u] : vb[u]));
+                    }
+                }
+                float2 p[kGsChunk];
+#pragma unroll
+                for (int u = 0; u < kGsChunk; ++u) p[u] = make_float2(acc[u].s, acc[u].c);
+                // transposing shuffle tree: after the exchanges at distances 16, 8 and 4 a
+                // lane holds value (lane >> 2) of its quad-group; distances 2 and 1 finish it
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool hi = (lane & 16u) != 0;
+                    const float2 keep = hi ? p[i + 4] : p[i], send = hi ? p[i] : p[i + 4];
+                    float2 r;
+                    r.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+                    r.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+                    p[i] = ff_add(keep, r);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const bool hi = (lane & 8u) != 0;
+                    const float2 keep = hi ? p[i + 2] : p[i], send = hi ? p[i] : p[i + 2];
+                    float2 r;
+                    r.x = __shfl_xor_sync(0xffffffffu, send.x, 8);
+                    r.y = __shfl_xor_sync(0xffffffffu, send.y, 8);
+                    p[i] = ff_add(keep, r);
+                }
+                float2 s;
+                {
+                    const bool hi = (lane & 4u) != 0;
+                    const float2 keep = hi ? p[1] : p[0], send = hi ? p[0] : p[1];
+                    float2 r;
+                    r.x = __shfl_xor_sync(0xffffffffu, send.x, 4);
+                    r.y = __shfl_xor_sync(0xffffffffu, send.y, 4);
+                    s = ff_add(keep, r);
+                }
+#pragma unroll
+                for (int o = 2; o > 0; o >>= 1) {
+                    float2 r;
+                    r.x = __shfl_xor_sync(0xffffffffu, s.x, o);
+                    r.y = __shfl_xor_sync(0xffffffffu, s.y, o);
+                    s = ff_add(s, r);
+                }
+                const int v = (int)(lane >> 2), u = v & 3;
+                if ((lane & 3u) == 0 && u < nk && (v < 4 || k0 + u < j)) {
+                    const int slot = (v < 4 ? 0 : 32) + k0 - 1 + u;
+                    accw[slot] = ff_add(accw[slot], s);
+                }
+            }
+        }
+        __syncthreads();
+        // block sums: warp q adds slot q (and slot 32 + q) over the 32 warps
+        {
+            const int wq = threadIdx.x >> 5;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int slot = wq + 32 * h;
+                if (h == 0 ? wq < j : wq < j - 1) {
+                    float2 b = red[lane * 64 + slot];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        float2 c;
+                        c.x = __shfl_down_sync(0xffffffffu, b.x, o);
+                        c.y = __shfl_down_sync(0xffffffffu, b.y, o);
+                        b = ff_add(b, c);
+                    }
+                    if (lane == 0) pA[(size_t)(h == 0 ? wq : kGsMaxJ + 1 + wq) * G + blockIdx.x] = b;
+                }
+            }
         }
     }
     gb.sync();
