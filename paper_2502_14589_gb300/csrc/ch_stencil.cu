@@ -941,19 +941,22 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
         accw[lane] = make_float2(0.f, 0.f);
         accw[32 + lane] = make_float2(0.f, 0.f);
         __syncwarp();
-        for (unsigned qa = q0; qa < NG; qa += 2u * S) {
-            const unsigned qb = qa + S;
-            const bool hb = qb < NG;
-            const bool fa = 4u * qa + 3u < N, fb = hb && 4u * qb + 3u < N;
+        // The tile loop runs the same number of trips in every thread of the block (the
+        // shuffle tree needs whole warps); threads past the grid's last group add zeros.
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (unsigned base = blockIdx.x * kArnThreads; base < NG; base += 2u * S) {
+            const unsigned qa = base + threadIdx.x, qb = qa + S;
+            const bool ha = qa < NG, hb = qb < NG;
+            const bool fa = ha && 4u * qa + 3u < N, fb = hb && 4u * qb + 3u < N;
             {
-                const float4 wa = stage2_group(qa);
-                st4(w, qa, fa, wa);
+                const float4 wa = ha ? stage2_group(qa) : zero4;
+                if (ha) st4(w, qa, fa, wa);
                 wsm[threadIdx.x] = wa;
-                xsm[threadIdx.x] = ld4(xj, qa, fa);
-                const float4 wb = hb ? stage2_group(qb) : make_float4(0.f, 0.f, 0.f, 0.f);
+                xsm[threadIdx.x] = ha ? ld4(xj, qa, fa) : zero4;
+                const float4 wb = hb ? stage2_group(qb) : zero4;
                 if (hb) st4(w, qb, fb, wb);
                 wsm[kArnThreads + threadIdx.x] = wb;
-                xsm[kArnThreads + threadIdx.x] = hb ? ld4(xj, qb, fb) : make_float4(0.f, 0.f, 0.f, 0.f);
+                xsm[kArnThreads + threadIdx.x] = hb ? ld4(xj, qb, fb) : zero4;
             }
             for (int cA = 0; cA < ncA; ++cA) {
                 const int k0 = 1 + (down ? ncA - 1 - cA : cA) * 4;
@@ -962,13 +965,13 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (u < nk && k0 + u < j) {
-                        va[u] = ld4(W(k0 + u), qa, fa);
-                        vb[u] = hb ? ld4(W(k0 + u), qb, fb) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        va[u] = ha ? ld4(W(k0 + u), qa, fa) : zero4;
+                        vb[u] = hb ? ld4(W(k0 + u), qb, fb) : zero4;
                     } else if (u < nk) {                    // column j is v_j itself
                         va[u] = xsm[threadIdx.x];
                         vb[u] = xsm[kArnThreads + threadIdx.x];
                     } else {
-                        va[u] = vb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        va[u] = vb[u] = zero4;
                     }
                 }
                 DotAcc<float> acc[kGsChunk];                  // [u]: W_k . w, [4 + u]: W_k . W_j

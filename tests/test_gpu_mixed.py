@@ -34,6 +34,8 @@ def host(t):
                                            (3, (32, 32, 32), 0.03, 1e-6),
                                            (2, (1024, 1024), 0.01, 1e-8),     # resident FP32 iteration
                                            (3, (144, 144, 144), 0.02, 1e-7),  # streaming FP32 iteration
+                                           # streaming, the last tile ending inside a warp
+                                           (2, (1400, 900), 0.01, 1e-8), (3, (110, 110, 105), 0.02, 1e-7),
                                            (2, (37, 53), 0.03, 1e-6),         # rows not a multiple of 4,
                                            (3, (10, 9, 11), 0.05, 1e-5)])     # partial last group
 def test_mixed_krylov_step(ch, oracle, dim, n, eps, tau):
