@@ -117,6 +117,41 @@ __device__ __forceinline__ void pair_diffs_inst(const Inst &I, const T *__restri
     }
 }
 
+// The same differences for the four consecutive points 4q..4q+3 of an instance whose rows
+// hold a multiple of four points (one row per group): 16-byte loads of the group's row and
+// of the neighbouring rows (planes), two scalars across the row ends, and per point the same
+// operations as pair_diffs_inst.
+template <int DIM>
+__device__ __forceinline__ void group_diffs_inst(const Inst &I, const float *__restrict__ x, unsigned q,
+                                                 float4 &xc, float4 (&d)[3]) {
+    const unsigned n0 = (unsigned)I.n[0], n1 = (unsigned)I.n[1];
+    const unsigned i = 4u * q, c0 = i % n0, r = i / n0, c1 = r % n1;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const unsigned r4 = n0 / 4u;                                  // float4s per row
+    xc = x4[q];
+    const float xl = x[c0 == 0u ? i + n0 - 1u : i - 1u];
+    const float xr = x[c0 + 4u == n0 ? i + 4u - n0 : i + 4u];
+    d[0] = make_float4((xc.x - xc.y) + (xc.x - xl), (xc.y - xc.z) + (xc.y - xc.x),
+                       (xc.z - xc.w) + (xc.z - xc.y), (xc.w - xr) + (xc.w - xc.z));
+    const float4 yp = x4[c1 + 1u == n1 ? q - (n1 - 1u) * r4 : q + r4];
+    const float4 ym = x4[c1 == 0u ? q + (n1 - 1u) * r4 : q - r4];
+    d[1] = make_float4((xc.x - yp.x) + (xc.x - ym.x), (xc.y - yp.y) + (xc.y - ym.y),
+                       (xc.z - yp.z) + (xc.z - ym.z), (xc.w - yp.w) + (xc.w - ym.w));
+    if (DIM == 3) {
+        const unsigned n2 = (unsigned)I.n[2], c2 = r / n1, p4 = r4 * n1;
+        const float4 zp = x4[c2 + 1u == n2 ? q - (n2 - 1u) * p4 : q + p4];
+        const float4 zm = x4[c2 == 0u ? q + (n2 - 1u) * p4 : q - p4];
+        d[2] = make_float4((xc.x - zp.x) + (xc.x - zm.x), (xc.y - zp.y) + (xc.y - zm.y),
+                           (xc.z - zp.z) + (xc.z - zm.z), (xc.w - zp.w) + (xc.w - zm.w));
+    } else {
+        d[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__device__ __forceinline__ float dot4f(const float4 &a, const float4 &b) {
+    return __fmaf_rn(a.w, b.w, __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x))));
+}
+
 template <typename VT> struct BDot;
 template <> struct BDot<double> {
     double s = 0.0;
@@ -294,6 +329,29 @@ kb_tstage(const Inst *insts, const Chunk *chunks, const Ctrl *ctrls, const VT *_
     if (!ctrls[ck.inst].active) return;
     const VT *xi = x + I.off;
     const VT k0 = (VT)I.kap[0], k1 = (VT)I.kap[1], k2 = (VT)I.kap[2];
+    if constexpr (sizeof(VT) == 4) {
+        if ((I.n[0] & 3) == 0) {      // rows of whole groups of four: 16-byte accesses
+            const float4 *D4 = reinterpret_cast<const float4 *>(D + I.off);
+            float4 *t4 = reinterpret_cast<float4 *>(t + I.off);
+            const unsigned ge = (unsigned)ck.end >> 2;
+            for (unsigned q = ((unsigned)ck.begin >> 2) + threadIdx.x; q < ge; q += blockDim.x) {
+                float4 xc, d[3];
+                group_diffs_inst<DIM>(I, xi, q, xc, d);
+                const float4 dq = D4[q];
+                float4 r = make_float4(dq.x * xc.x, dq.y * xc.y, dq.z * xc.z, dq.w * xc.w);
+                r.x = fmaf(k0, d[0].x, r.x); r.y = fmaf(k0, d[0].y, r.y);
+                r.z = fmaf(k0, d[0].z, r.z); r.w = fmaf(k0, d[0].w, r.w);
+                r.x = fmaf(k1, d[1].x, r.x); r.y = fmaf(k1, d[1].y, r.y);
+                r.z = fmaf(k1, d[1].z, r.z); r.w = fmaf(k1, d[1].w, r.w);
+                if (DIM == 3) {
+                    r.x = fmaf(k2, d[2].x, r.x); r.y = fmaf(k2, d[2].y, r.y);
+                    r.z = fmaf(k2, d[2].z, r.z); r.w = fmaf(k2, d[2].w, r.w);
+                }
+                t4[q] = r;
+            }
+            return;
+        }
+    }
     // FP64: pair-sum form with D; FP32: difference form with J (no cancellation of the
     // eps^2 sigma x term or of the smooth part of the neighbour sums in FP32 rounding)
     CHUNK_LOOP(l) {
@@ -449,6 +507,131 @@ kbg_stage2A(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, const float *__
     const float gam = (float)ctrl->gam[j - 1];
     const float c1 = gam * (float)I.s[0], c2 = gam * (float)I.s[1], c3 = gam * (float)I.s[2];
     const float *ti = t + I.off;
+    const float *xj = W(j);
+    float2 *part = gpart + (size_t)blockIdx.x * kBGsSlots;
+    if ((I.n[0] & 3) == 0) {
+        // ---- rows of whole groups of four: stage 2 fused into round A.  Tiles of two groups
+        //      per thread; the tile's w is written once and kept with v_j in shared memory
+        //      while the columns pass (v_j serves as column j), and the per-thread partials of
+        //      each (tile, four columns) are added across the warp by a transposing shuffle
+        //      tree into the warp's slots (c_k in [0, 32), G_jk in [32, 64)).
+        __shared__ float4 wsm[2][kThreads], xsm[2][kThreads];
+        __shared__ float2 accw[kThreads / 32][kBGsSlots];
+        const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+        accw[wid][lane] = make_float2(0.f, 0.f);
+        accw[wid][32 + lane] = make_float2(0.f, 0.f);
+        __syncwarp();
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 *x4 = reinterpret_cast<const float4 *>(xj + I.off);
+        float4 *w4 = reinterpret_cast<float4 *>(w + I.off);
+        auto stage2 = [&](unsigned q) -> float4 {
+            float4 tc, d[3];
+            group_diffs_inst<DIM>(I, ti, q, tc, d);
+            float4 r = make_float4(c1 * d[0].x, c1 * d[0].y, c1 * d[0].z, c1 * d[0].w);
+            r.x = fmaf(c2, d[1].x, r.x); r.y = fmaf(c2, d[1].y, r.y);
+            r.z = fmaf(c2, d[1].z, r.z); r.w = fmaf(c2, d[1].w, r.w);
+            if (DIM == 3) {
+                r.x = fmaf(c3, d[2].x, r.x); r.y = fmaf(c3, d[2].y, r.y);
+                r.z = fmaf(c3, d[2].z, r.z); r.w = fmaf(c3, d[2].w, r.w);
+            }
+            return r;
+        };
+        const unsigned gb = (unsigned)ck.begin >> 2, ge = (unsigned)ck.end >> 2;
+        // the same number of trips in every thread (the shuffle tree needs whole warps)
+        for (unsigned base = gb; base < ge; base += 2u * kThreads) {
+            const unsigned qa = base + threadIdx.x, qb = qa + kThreads;
+            const bool ha = qa < ge, hb = qb < ge;
+            const float4 wa = ha ? stage2(qa) : zero4, wb = hb ? stage2(qb) : zero4;
+            if (ha) w4[qa] = wa;
+            if (hb) w4[qb] = wb;
+            wsm[0][threadIdx.x] = wa;
+            wsm[1][threadIdx.x] = wb;
+            xsm[0][threadIdx.x] = ha ? x4[qa] : zero4;
+            xsm[1][threadIdx.x] = hb ? x4[qb] : zero4;
+            for (int k0 = 1; k0 <= j; k0 += 4) {
+                const int nk = min(4, j - k0 + 1);
+                float4 va[4], vb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (u < nk && k0 + u < j) {
+                        const float4 *c4 = reinterpret_cast<const float4 *>(W(k0 + u) + I.off);
+                        va[u] = ha ? c4[qa] : zero4;
+                        vb[u] = hb ? c4[qb] : zero4;
+                    } else if (u < nk) {                    // column j is v_j itself
+                        va[u] = xsm[0][threadIdx.x];
+                        vb[u] = xsm[1][threadIdx.x];
+                    } else {
+                        va[u] = vb[u] = zero4;
+                    }
+                }
+                float2 p[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) p[q] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float4 wv = wsm[r][threadIdx.x], xv = xsm[r][threadIdx.x];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        bgs_acc(p[u], dot4f(wv, r == 0 ? va[u] : vb[u]));
+                        bgs_acc(p[4 + u], dot4f(xv, r == 0 ? va[u] : vb[u]));
+                    }
+                }
+                // after the exchanges at lane distances 16, 8 and 4 a lane holds value
+                // (lane >> 2) of its group of four lanes; distances 2 and 1 finish the sum
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool hi = (lane & 16u) != 0;
+                    const float2 keep = hi ? p[i + 4] : p[i], send = hi ? p[i] : p[i + 4];
+                    float2 rv;
+                    rv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+                    rv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+                    p[i] = ch::ff_add(keep, rv);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const bool hi = (lane & 8u) != 0;
+                    const float2 keep = hi ? p[i + 2] : p[i], send = hi ? p[i] : p[i + 2];
+                    float2 rv;
+                    rv.x = __shfl_xor_sync(0xffffffffu, send.x, 8);
+                    rv.y = __shfl_xor_sync(0xffffffffu, send.y, 8);
+                    p[i] = ch::ff_add(keep, rv);
+                }
+                float2 sv;
+                {
+                    const bool hi = (lane & 4u) != 0;
+                    const float2 keep = hi ? p[1] : p[0], send = hi ? p[0] : p[1];
+                    float2 rv;
+                    rv.x = __shfl_xor_sync(0xffffffffu, send.x, 4);
+                    rv.y = __shfl_xor_sync(0xffffffffu, send.y, 4);
+                    sv = ch::ff_add(keep, rv);
+                }
+#pragma unroll
+                for (int o = 2; o > 0; o >>= 1) {
+                    float2 rv;
+                    rv.x = __shfl_xor_sync(0xffffffffu, sv.x, o);
+                    rv.y = __shfl_xor_sync(0xffffffffu, sv.y, o);
+                    sv = ch::ff_add(sv, rv);
+                }
+                const int v = (int)(lane >> 2), u = v & 3;
+                if ((lane & 3u) == 0 && u < nk && (v < 4 || k0 + u < j)) {
+                    const int slot = (v < 4 ? 0 : 32) + k0 - 1 + u;
+                    accw[wid][slot] = ch::ff_add(accw[wid][slot], sv);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < kBGsSlots) {          // the chunk's partials, warps added in order
+            const int v = threadIdx.x, k = v < 32 ? v : v - 32;
+            if (v < 32 ? k < j : k < j - 1) {
+                float2 a = accw[0][v];
+#pragma unroll
+                for (int q = 1; q < kThreads / 32; ++q) a = ch::ff_add(a, accw[q][v]);
+                part[v] = a;
+                __threadfence();
+            }
+        }
+        __syncthreads();
+    } else {
     // ---- stage 2: w = gam_j A t (difference form, FP32)
     CHUNK_LOOP(l) {
         float q[3];
@@ -460,8 +643,6 @@ kbg_stage2A(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, const float *__
     }
     // ---- round A: per-chunk partials of W_k . w (k <= j) and W_j . W_k (k < j), four
     //      columns per sweep over this thread's points (its own w values: no barrier)
-    const float *xj = W(j);
-    float2 *part = gpart + (size_t)blockIdx.x * kBGsSlots;
     __shared__ float2 bout[8];
     for (int k0 = 1; k0 <= j; k0 += 4) {
         const int nk = min(4, j - k0 + 1);
@@ -485,6 +666,7 @@ kbg_stage2A(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, const float *__
                 part[k0 - 1 + u] = bout[u];
                 if (k0 + u < j) part[32 + k0 - 1 + u] = bout[4 + u];
             }
+    }
     }
     // ---- the instance's last chunk: sums over its chunks in order, then h_kj
     __shared__ bool last;
@@ -577,6 +759,31 @@ kbg_roundB(const Inst *insts, const Chunk *chunks, Ctrl *ctrls, float *__restric
     float2 acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+    if ((I.n[0] & 3) == 0) {          // rows of whole groups of four: 16-byte accesses
+        float4 *w4 = reinterpret_cast<float4 *>(w + I.off);
+        const unsigned ge = (unsigned)ck.end >> 2;
+        for (unsigned q = ((unsigned)ck.begin >> 2) + threadIdx.x; q < ge; q += blockDim.x) {
+            float4 x = w4[q];
+            for (int k0 = 1; k0 <= j; k0 += 8) {       // eight column loads in flight
+                float4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    v[u] = k0 + u <= j ? reinterpret_cast<const float4 *>(W(k0 + u) + I.off)[q]
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (k0 + u <= j) {
+                        const float a_ = -as[k0 + u - 1];
+                        x.x = __fmaf_rn(a_, v[u].x, x.x);
+                        x.y = __fmaf_rn(a_, v[u].y, x.y);
+                        x.z = __fmaf_rn(a_, v[u].z, x.z);
+                        x.w = __fmaf_rn(a_, v[u].w, x.w);
+                    }
+            }
+            w4[q] = x;
+            bgs_acc(acc[0], dot4f(x, x));
+        }
+    } else
     CHUNK_LOOP(l) {
         const int64_t gi = I.off + l;
         float x = w[gi];

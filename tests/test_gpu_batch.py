@@ -69,6 +69,25 @@ def test_mixed_batch_error_at_T(ch, oracle):
         assert abs(ys[i].mean() - y0s[i].mean()) < 1e-13
 
 
+@pytest.mark.parametrize("dim,sizes,eps", [
+    (2, [(36, 36), (50, 50), (100, 100), (44, 60)], [0.03, 0.02, 0.015, 0.04]),
+    (3, [(12, 12, 12), (16, 12, 20), (10, 10, 10)], [0.05, 0.04, 0.06])])
+def test_mixed_batch_grouped_and_scalar_rows(ch, oracle, dim, sizes, eps):
+    """Instances whose rows hold a multiple of four points take the 16-byte grouped kernels
+    (a chunk's last tile ending inside a warp: 36^2 = 1296 points is 1024 + 272); the others
+    (50, 10) take the scalar ones, in the same batch.  Each is held to the mixed bound."""
+    y0s = [inputs.initial_state(n, 70 + i) for i, n in enumerate(sizes)]
+    T = 3e-5 if dim == 2 else 2e-5
+    ys, st, chunk = run_batch(ch, dim, [list(n) for n in sizes], eps, y0s, ch.CH_MIXED, T, tol=1e-6)
+    for i, n in enumerate(sizes):
+        yo, sto = oracle_run(oracle, dim, n, eps[i], y0s[i], T, tol=1e-6)
+        err = np.linalg.norm(ys[i] - yo) / np.linalg.norm(yo)
+        print(f"mixed batch instance {i} n={n}: steps {st[i]['steps']} vs {sto['steps']}, error at T {err:.2e}")
+        assert st[i]["t"] == T
+        assert err < 1e-5
+        assert abs(ys[i].mean() - y0s[i].mean()) < 1e-13
+
+
 def test_batch_3d_and_stationary_instance(ch, oracle):
     sides = [12, 16, 10]
     eps = [0.05, 0.04, 0.06]
