@@ -130,13 +130,20 @@ __device__ double *expm_block(int n, PhiWork &W, const MM &mm) {
         X4[e] = v + T4[e];                              // Q = V + U
     }
     __syncthreads();
-    // Gauss-Jordan with partial pivoting on [P | Q]: Q <- P^{-1} Q
+    // Gauss-Jordan with partial pivoting on [P | Q]: Q <- P^{-1} Q.  Two barriers per column:
+    // warp 0 finds the pivot row pv and stages, in the free buffers T4 and T5, the scaled
+    // pivot row, the old row k and the multipliers; then every element is updated in place,
+    // rows k and pv exchanging their roles (the same operations as swapping the rows, scaling
+    // row k and eliminating).  Columns left of k of P are zero outside the unit entries and
+    // are not touched.
     double *P = X2, *Q = X4;
+    double *prowP = T4, *prowQ = T4 + n, *rowkP = T5, *rowkQ = T5 + n;   // 2n <= n*n for n >= 2
     for (int k = 0; k < n; ++k) {
         if (threadIdx.x < 32) {
+            const int lane = (int)threadIdx.x;
             double best = -1.0;
             int bi = k;
-            for (int i = k + (int)threadIdx.x; i < n; i += 32) {
+            for (int i = k + lane; i < n; i += 32) {
                 const double a = fabs(P[i * n + k]);
                 if (a > best) { best = a; bi = i; }
             }
@@ -145,32 +152,30 @@ __device__ double *expm_block(int n, PhiWork &W, const MM &mm) {
                 const int oi = __shfl_down_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
-            if (threadIdx.x == 0) W.piv = bi;
+            const int pv = __shfl_sync(0xffffffffu, bi, 0);
+            const double pinv = 1.0 / P[pv * n + k];
+            for (int c = lane; c < n; c += 32) {
+                prowP[c] = P[pv * n + c] * pinv;
+                prowQ[c] = Q[pv * n + c] * pinv;
+                rowkP[c] = P[k * n + c];
+                rowkQ[c] = Q[k * n + c];
+                W.fcol[c] = c == pv ? P[k * n + k] : P[c * n + k];
+            }
+            if (lane == 0) W.piv = pv;
         }
         __syncthreads();
         const int pv = W.piv;
-        if (pv != k) {
-            for (int cc = threadIdx.x; cc < n; cc += blockDim.x) {
-                double t = P[k * n + cc]; P[k * n + cc] = P[pv * n + cc]; P[pv * n + cc] = t;
-                t = Q[k * n + cc]; Q[k * n + cc] = Q[pv * n + cc]; Q[pv * n + cc] = t;
-            }
-            __syncthreads();
-        }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) W.fcol[i] = P[i * n + k];
-        if (threadIdx.x == 0) W.pinv = 1.0 / P[k * n + k];
-        __syncthreads();
-        const double pinv = W.pinv;
-        for (int cc = threadIdx.x; cc < n; cc += blockDim.x) {
-            P[k * n + cc] *= pinv;
-            Q[k * n + cc] *= pinv;
-        }
-        __syncthreads();
         for (int e = threadIdx.x; e < nn; e += blockDim.x) {
             const int i = e / n, cc = e - i * n;
-            if (i == k) continue;
-            const double f = W.fcol[i];
-            if (cc >= k) P[e] = fma(-f, P[k * n + cc], P[e]);
-            Q[e] = fma(-f, Q[k * n + cc], Q[e]);
+            if (i == k) {
+                if (cc >= k) P[e] = prowP[cc];
+                Q[e] = prowQ[cc];
+            } else {
+                const double f = W.fcol[i];
+                const double p0 = i == pv ? rowkP[cc] : P[e], q0 = i == pv ? rowkQ[cc] : Q[e];
+                if (cc >= k) P[e] = fma(-f, prowP[cc], p0);
+                Q[e] = fma(-f, prowQ[cc], q0);
+            }
         }
         __syncthreads();
     }
