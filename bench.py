@@ -252,6 +252,7 @@ def batch_compare(wl, rank, dist, T=None, warmup=1, steps=1, plain=True):
         yh = y.cpu().numpy()
         ys[name] = [yh[offs[i]:offs[i] + Ns[i]] for i in range(count)]
         out[name] = {"ms_to_T": ms / steps, "value": ops / (ms * 1e-3), "chunk_len": chunk,
+                     "scheduling_groups": ch.ch_batch_groups(h),
                      "batch_steps": max(x["steps"] for x in st), "kernel_launches": launches // steps}
         ch.ch_destroy_batch(h)
     if plain:

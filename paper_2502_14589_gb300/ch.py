@@ -112,6 +112,8 @@ def load():
         L.ch_kernel_launches.argtypes = [_P]
         L.ch_batch_kernel_launches.restype = C.c_int64
         L.ch_batch_kernel_launches.argtypes = [_P]
+        L.ch_batch_groups.restype = C.c_int
+        L.ch_batch_groups.argtypes = [_P]
         _LIB = L
     return _LIB
 
@@ -400,6 +402,10 @@ def ch_integrate_batch(h, prm, y, count):
 
 def ch_batch_kernel_launches(h):
     return load().ch_batch_kernel_launches(h)
+
+
+def ch_batch_groups(h):
+    return load().ch_batch_groups(h)
 
 
 def ch_energy_mass_noalloc(dim, n, eps, y, out, stream=None):

@@ -992,6 +992,18 @@ struct ch_batch {
     int64_t launches;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (slot, j) -> iteration graph
     int mmax_graphs;
+    // pinned copies read back at the end of a device-driven run
+    BState *hbs;                            // count per-instance states
+    long long *hsteps;                      // batch steps taken
+    unsigned long long *hran;               // kernels executed
+    // Scheduling groups: a batch whose few stiffest instances would set its time runs them as
+    // a group of their own, concurrently with the others, each group a batch object on its
+    // own stream (the stiff group's of the highest priority) sharing the caller's layout.
+    int ngroups;                            // 0: no groups (this object runs its instances)
+    ch_batch *grp[2];
+    std::vector<int> grp_idx[2];            // instance of this batch behind each group instance
+    cudaStream_t grp_stream[2];
+    cudaEvent_t grp_ev[3];
 };
 
 namespace {
@@ -1297,8 +1309,10 @@ ch_status build_run_graph(ch_batch *b, const ch_params *prm, double *y) {
     return CH_OK;
 }
 
+// Device-driven run, queued on the batch's stream: nothing here waits for the GPU, so the
+// groups of a batch run concurrently.  finish_b_dev waits and reads the counters.
 template <typename VT>
-ch_status integrate_b_dev(ch_batch *b, const ch_params *prm, double *y, ch_stats *stats) {
+ch_status launch_b_dev(ch_batch *b, const ch_params *prm, double *y) {
     cudaStream_t s = b->stream;
     BTRY(build_run_graph<VT>(b, prm, y));
     kb_init<<<(b->count + 255) / 256, 256, 0, s>>>(b->bs, b->ctrls, b->count, prm->tau0);
@@ -1307,17 +1321,19 @@ ch_status integrate_b_dev(ch_batch *b, const ch_params *prm, double *y, ch_stats
     rhs_b<VT>(b, s, y, 0, 0, nullptr, nullptr);                      // f(y^0), norms
     BCUDA(cudaGetLastError());
     BCUDA(cudaGraphLaunch(b->run_exec, s));
-    long long steps = 0;
-    unsigned long long ran = 0;
     BCUDA(cudaMemcpyAsync(&b->hflags[2], &b->dflags[1], sizeof(int), cudaMemcpyDeviceToHost, s));
-    BCUDA(cudaMemcpyAsync(&steps, b->dsteps, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    BCUDA(cudaMemcpyAsync(&ran, b->dlaunch, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    std::vector<BState> hb(b->count);
-    BCUDA(cudaMemcpyAsync(hb.data(), b->bs, b->count * sizeof(BState), cudaMemcpyDeviceToHost, s));
-    BCUDA(cudaStreamSynchronize(s));
-    b->launches += 3 + (int64_t)ran;            // kb_init, f(y^0) and the graph's executed kernels
+    BCUDA(cudaMemcpyAsync(b->hsteps, b->dsteps, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    BCUDA(cudaMemcpyAsync(b->hran, b->dlaunch, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    BCUDA(cudaMemcpyAsync(b->hbs, b->bs, b->count * sizeof(BState), cudaMemcpyDeviceToHost, s));
+    return CH_OK;
+}
+
+ch_status finish_b_dev(ch_batch *b, ch_stats *stats) {
+    BCUDA(cudaStreamSynchronize(b->stream));
+    b->launches += 3 + (int64_t)*b->hran;       // kb_init, f(y^0) and the graph's executed kernels
     ch_status rc = CH_OK;
     if (b->hflags[2] != 0) rc = bfail(CH_ENOTCONV, "max_steps reached before T");
+    const BState *hb = b->hbs;
     for (int i = 0; i < b->count; ++i) {
         if (hb[i].status && rc == CH_OK)
             rc = bfail((ch_status)hb[i].status, "instance %d failed (status %d) at t = %g", i, hb[i].status, hb[i].t);
@@ -1331,6 +1347,12 @@ ch_status integrate_b_dev(ch_batch *b, const ch_params *prm, double *y, ch_stats
         }
     }
     return rc;
+}
+
+template <typename VT>
+ch_status integrate_b_dev(ch_batch *b, const ch_params *prm, double *y, ch_stats *stats) {
+    BTRY(launch_b_dev<VT>(b, prm, y));
+    return finish_b_dev(b, stats);
 }
 
 // Chunk length candidates for the autotuner (values per chunk; a chunk is one thread block).
@@ -1353,6 +1375,16 @@ extern "C" {
 
 ch_status ch_destroy_batch(ch_batch *b) {
     if (!b) return CH_OK;
+    if (b->ngroups) {
+        for (int g = 0; g < 2; ++g) {
+            ch_destroy_batch(b->grp[g]);
+            if (b->grp_stream[g]) cudaStreamDestroy(b->grp_stream[g]);
+        }
+        for (int k = 0; k < 3; ++k)
+            if (b->grp_ev[k]) cudaEventDestroy(b->grp_ev[k]);
+        delete b;
+        return CH_OK;
+    }
     cudaStreamSynchronize(b->stream);
     void *bufs[] = {b->insts, b->chunks, b->bs, b->ctrls, b->H, b->u, b->ynew, b->F[0], b->F[1],
                     b->mu, b->q, b->partials, b->tickets, b->D, b->t, b->V, b->W[0], b->W[1],
@@ -1360,6 +1392,9 @@ ch_status ch_destroy_batch(ch_batch *b) {
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (b->hflags) cudaFreeHost(b->hflags);
+    if (b->hbs) cudaFreeHost(b->hbs);
+    if (b->hsteps) cudaFreeHost(b->hsteps);
+    if (b->hran) cudaFreeHost(b->hran);
     for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
     if (b->ev[0]) cudaEventDestroy(b->ev[0]);
     if (b->ev[1]) cudaEventDestroy(b->ev[1]);
@@ -1370,8 +1405,12 @@ ch_status ch_destroy_batch(ch_batch *b) {
     return CH_OK;
 }
 
-ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *eps, int precision,
-                          int mmax_capacity, void *cuda_stream, ch_batch **out) {
+// One batch object.  With ext_off the instances keep the given offsets in an array of
+// ext_total values (a scheduling group of a larger batch, sharing the caller's layout);
+// every per-point workspace then spans ext_total values.
+static ch_status create_impl(int dim, int count, const int64_t *n, const double *eps, int precision,
+                             int mmax_capacity, void *cuda_stream, const int64_t *ext_off,
+                             int64_t ext_total, ch_batch **out) {
     if (!out || !n || !eps) return bfail(CH_EINVAL, "null argument");
     *out = nullptr;
     if (dim != 2 && dim != 3) return bfail(CH_EINVAL, "dim must be 2 or 3");
@@ -1400,7 +1439,7 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
         }
         if (!(eps[i] > 0.0) || !isfinite(eps[i])) { delete b; return bfail(CH_EINVAL, "instance %d: eps must be > 0", i); }
         I.N = N;
-        I.off = off;
+        I.off = ext_off ? ext_off[i] : off;
         I.eps2 = eps[i] * eps[i];
         I.sigma = 0.0;
         for (int a = 0; a < dim; ++a) {
@@ -1408,13 +1447,14 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
             I.kap[a] = I.eps2 * I.s[a];
             I.sigma += 2.0 * I.s[a];
         }
-        b->offsets[i] = off;
+        b->offsets[i] = I.off;
         off += (N + 63) / 64 * 64;
         if (off >= ((int64_t)1 << 31)) {   // checked per instance, before the sum can overflow
             delete b;
             return bfail(CH_EINVAL, "batch of more than 2^31 - 1 values (at instance %d)", i);
         }
     }
+    if (ext_off) off = ext_total;
     b->offsets[count] = off;
     b->Ntot = off;
     if (off >= ((int64_t)1 << 31)) { delete b; return bfail(CH_EINVAL, "batch of %lld values exceeds 2^31 - 1", (long long)off); }
@@ -1461,6 +1501,9 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
     if (e == cudaSuccess) e = cudaMemset(b->ctrls, 0, sizeof(Ctrl) * count);
     if (e == cudaSuccess) e = cudaMemset(b->H, 0, sizeof(double) * count * (size_t)(mmax_capacity + 1) * mmax_capacity);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->hflags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->hbs, sizeof(BState) * count);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->hsteps, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->hran, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[1], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
@@ -1525,6 +1568,93 @@ ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *ep
     return CH_OK;
 }
 
+// Scheduling groups.  The time of a batch is set by its stiffest instances: they take the
+// most steps, each a Krylov run of iterations on a small part of the batch, bound by latency
+// rather than bandwidth, while the rest of the batch is bandwidth-bound.  So a batch of at
+// least kGroupMinCount instances whose instances within a factor 2 of the largest stiffness
+// estimate are at most an eighth of it runs those as a second batch, concurrently with the
+// rest on a stream of higher priority.  Stiffness estimate: the dominant terms of the closed
+// form of ||A_hat||_1 at d = -1 (Sec. 3.2), eps^2 (sum_a 4 n_a^2)^2 + sum_a 4 n_a^2.
+// CH_BATCH_GROUPS=1 keeps every batch in one group.
+constexpr int kGroupMinCount = 16;
+
+ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *eps, int precision,
+                          int mmax_capacity, void *cuda_stream, ch_batch **out) {
+    const char *env = getenv("CH_BATCH_GROUPS");
+    bool valid = out && n && eps && (dim == 2 || dim == 3) && count >= kGroupMinCount && count <= 65536 &&
+                 !(env && env[0] == '1');
+    std::vector<double> lam;
+    std::vector<int64_t> offs;
+    if (valid) {
+        lam.resize(count);
+        offs.resize(count + 1);
+        int64_t off = 0;
+        for (int i = 0; i < count && valid; ++i) {
+            int64_t N = 1;
+            double s4 = 0.0;
+            for (int a = 0; a < dim; ++a) {
+                const int64_t na = n[3 * i + a];
+                if (na < 4 || na > (1 << 20)) { valid = false; break; }
+                N *= na;
+                s4 += 4.0 * (double)na * (double)na;
+            }
+            if (!(eps[i] > 0.0) || !isfinite(eps[i])) valid = false;
+            lam[i] = eps[i] * eps[i] * s4 * s4 + s4;
+            offs[i] = off;
+            off += (N + 63) / 64 * 64;
+            if (off >= ((int64_t)1 << 31)) valid = false;
+        }
+        offs[count] = off;
+    }
+    std::vector<int> stiff, rest;
+    if (valid) {
+        const double lmax = *std::max_element(lam.begin(), lam.end());
+        for (int i = 0; i < count; ++i) (lam[i] >= 0.5 * lmax ? stiff : rest).push_back(i);
+        valid = !stiff.empty() && (int)stiff.size() * 8 <= count;
+    }
+    if (!valid)
+        return create_impl(dim, count, n, eps, precision, mmax_capacity, cuda_stream, nullptr, 0, out);
+    *out = nullptr;
+    ch_batch *b = new ch_batch();
+    b->dim = dim; b->count = count; b->precision = precision; b->mmax_cap = mmax_capacity;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->offsets = offs;
+    b->Ntot = offs[count];
+    b->ngroups = 2;
+    b->grp_idx[0] = stiff;
+    b->grp_idx[1] = rest;
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->grp_stream[0], cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->grp_stream[1], cudaStreamNonBlocking, least);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->grp_ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        ch_destroy_batch(b);
+        return bfail(CH_ECUDA, "batch group streams: %s", cudaGetErrorString(e));
+    }
+    for (int g = 0; g < 2; ++g) {
+        const std::vector<int> &idx = b->grp_idx[g];
+        std::vector<int64_t> ng(3 * idx.size()), og(idx.size());
+        std::vector<double> eg(idx.size());
+        for (size_t k = 0; k < idx.size(); ++k) {
+            for (int a = 0; a < 3; ++a) ng[3 * k + a] = n[3 * idx[k] + a];
+            eg[k] = eps[idx[k]];
+            og[k] = offs[idx[k]];
+        }
+        const ch_status st = create_impl(dim, (int)idx.size(), ng.data(), eg.data(), precision, mmax_capacity,
+                                         b->grp_stream[g], og.data(), b->Ntot, &b->grp[g]);
+        if (st != CH_OK) {
+            ch_destroy_batch(b);
+            return st;
+        }
+    }
+    b->chunk_len = b->grp[1]->chunk_len;
+    *out = b;
+    return CH_OK;
+}
+
+int ch_batch_groups(const ch_batch *b) { return b ? (b->ngroups ? b->ngroups : 1) : 0; }
+
 ch_status ch_batch_layout(const ch_batch *b, int64_t *offsets, int *chunk_len) {
     if (!b) return bfail(CH_EINVAL, "null batch");
     if (offsets)
@@ -1544,11 +1674,41 @@ ch_status ch_integrate_batch(ch_batch *b, const ch_params *prm, double *y, ch_st
     if (prm->mmax < 1 || prm->mmax > b->mmax_cap) return bfail(CH_EINVAL, "mmax outside [1, capacity]");
     if (prm->max_steps < 1) return bfail(CH_EINVAL, "max_steps must be >= 1");
     ch::NvtxRange range("ch_integrate_batch EE2");
+    const char *env = getenv("CH_BATCH_HOST_LOOP");
+    const bool host_loop = env && env[0] == '1';
+    if (b->ngroups) {
+        // both groups start after the caller's earlier work on its stream, run concurrently,
+        // and the caller's stream waits for both
+        BCUDA(cudaEventRecord(b->grp_ev[2], b->stream));
+        for (int g = 0; g < 2; ++g) BCUDA(cudaStreamWaitEvent(b->grp_stream[g], b->grp_ev[2], 0));
+        std::vector<ch_stats> gst[2];
+        ch_status rc[2] = {CH_OK, CH_OK};
+        bool queued[2] = {false, false};
+        for (int g = 0; g < 2; ++g) {
+            gst[g].resize(b->grp[g]->count);
+            if (host_loop) continue;
+            rc[g] = b->precision == CH_MIXED ? launch_b_dev<float>(b->grp[g], prm, y)
+                                             : launch_b_dev<double>(b->grp[g], prm, y);
+            queued[g] = rc[g] == CH_OK;
+        }
+        for (int g = 0; g < 2; ++g) {
+            if (queued[g]) rc[g] = finish_b_dev(b->grp[g], gst[g].data());
+            else if (host_loop || (rc[g] == CH_ECUDA && !b->grp[g]->run_exec))
+                rc[g] = b->precision == CH_MIXED ? integrate_b<float>(b->grp[g], prm, y, gst[g].data())
+                                                 : integrate_b<double>(b->grp[g], prm, y, gst[g].data());
+        }
+        for (int g = 0; g < 2; ++g) {
+            BCUDA(cudaEventRecord(b->grp_ev[g], b->grp_stream[g]));
+            BCUDA(cudaStreamWaitEvent(b->stream, b->grp_ev[g], 0));
+            if (stats)
+                for (size_t k = 0; k < b->grp_idx[g].size(); ++k) stats[b->grp_idx[g][k]] = gst[g][k];
+        }
+        return rc[0] != CH_OK ? rc[0] : rc[1];
+    }
     // The run is one graph launch (device-driven steps and Krylov iterations); CH_BATCH_HOST_LOOP=1
     // selects the host-driven loop (one graph per Arnoldi iteration, the host reading a
     // device flag after each), which is also taken if the run graph cannot be built.
-    const char *env = getenv("CH_BATCH_HOST_LOOP");
-    if (!(env && env[0] == '1')) {
+    if (!host_loop) {
         const ch_status st = b->precision == CH_MIXED ? integrate_b_dev<float>(b, prm, y, stats)
                                                       : integrate_b_dev<double>(b, prm, y, stats);
         if (st != CH_ECUDA || b->run_exec) return st;
@@ -1557,6 +1717,9 @@ ch_status ch_integrate_batch(ch_batch *b, const ch_params *prm, double *y, ch_st
                                     : integrate_b<double>(b, prm, y, stats);
 }
 
-int64_t ch_batch_kernel_launches(const ch_batch *b) { return b ? b->launches : 0; }
+int64_t ch_batch_kernel_launches(const ch_batch *b) {
+    if (!b) return 0;
+    return b->ngroups ? b->grp[0]->launches + b->grp[1]->launches : b->launches;
+}
 
 }  // extern "C"

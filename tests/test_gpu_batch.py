@@ -181,3 +181,52 @@ def test_device_driven_run_stops_at_max_steps(ch, monkeypatch):
     assert rcd == rch == ch.CH_ENOTCONV
     for a, b in zip(yd, yh):
         assert np.array_equal(a, b)
+
+
+def _group_batch():
+    """18 soft instances and 2 stiff ones (stiffness estimate 20x larger): two groups.  No
+    instance exceeds 1024 points, so every chunk length the creation-time tuner may pick gives
+    one chunk per instance and the same reduction order in every run."""
+    sides = [16, 20, 24] * 6 + [32, 32]
+    eps = [0.01 + 0.0005 * i for i in range(18)] + [0.05, 0.048]
+    y0s = [inputs.initial_state((s, s), 80 + i) for i, s in enumerate(sides)]
+    return sides, eps, y0s
+
+
+def test_batch_scheduling_groups_fp64_match_oracle(ch, oracle):
+    """The stiff group runs concurrently with the rest; every instance still follows the
+    oracle's step sequence exactly (steps and matvecs) and its state to 1e-10."""
+    sides, eps, y0s = _group_batch()
+    h = ch.ch_create_batch(2, sides, eps, ch.CH_FP64, 30)
+    try:
+        assert ch.ch_batch_groups(h) == 2
+    finally:
+        ch.ch_destroy_batch(h)
+    T = 3e-5
+    ys, st, chunk = run_batch(ch, 2, sides, eps, y0s, ch.CH_FP64, T)
+    for i, s in enumerate(sides):
+        yo, sto = oracle_run(oracle, 2, (s, s), eps[i], y0s[i], T)
+        err = np.linalg.norm(ys[i] - yo) / np.linalg.norm(yo)
+        assert st[i]["t"] == T
+        assert st[i]["steps"] == sto["steps"], (i, st[i], sto)
+        assert st[i]["matvecs"] == sto["matvecs"], (i, st[i], sto)
+        assert err < 1e-10, (i, err)
+
+
+def test_batch_scheduling_groups_mixed_device_equals_host_loop(ch, monkeypatch):
+    """Concurrent groups (device-driven) and the host-driven loop running the groups one
+    after the other give bit-identical states and counters; CH_BATCH_GROUPS=1 keeps one
+    group."""
+    sides, eps, y0s = _group_batch()
+    yd, sd, rcd, _ = _run_with_loop(ch, monkeypatch, False, sides, eps, y0s, ch.CH_MIXED, 2e-5)
+    yh, sh, rch, _ = _run_with_loop(ch, monkeypatch, True, sides, eps, y0s, ch.CH_MIXED, 2e-5)
+    assert rcd == rch == 0
+    for i in range(len(sides)):
+        np.testing.assert_array_equal(yd[i], yh[i])
+        assert sd[i]["steps"] == sh[i]["steps"] and sd[i]["matvecs"] == sh[i]["matvecs"]
+    monkeypatch.setenv("CH_BATCH_GROUPS", "1")
+    h = ch.ch_create_batch(2, sides, eps, ch.CH_MIXED, 30)
+    try:
+        assert ch.ch_batch_groups(h) == 1
+    finally:
+        ch.ch_destroy_batch(h)
