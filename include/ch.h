@@ -223,13 +223,14 @@ ch_status ch_batch_layout(const ch_batch *b, int64_t *offsets, int *chunk_len);
  * steps are counted per scheduling group (below).                                         */
 ch_status ch_integrate_batch(ch_batch *b, const ch_params *prm, double *y, ch_stats *stats);
 int64_t ch_batch_kernel_launches(const ch_batch *b);
-/* Scheduling groups of the batch (1 or 2; 0 for NULL).  A batch of at least 16 instances
- * whose instances within a factor 2 of the largest stiffness estimate eps^2 (sum_a 4 n_a^2)^2
- * + sum_a 4 n_a^2 (the leading terms of ||A_hat||_1 at d = -1, Sec. 3.2) number at most an
- * eighth of it integrates those as a second group, concurrently with the others, on a
- * stream of higher priority; both groups start after earlier work on the batch's stream and
- * the batch's stream waits for both.  Each instance's arithmetic does not depend on its
- * group.  The environment variable CH_BATCH_GROUPS=1, read at creation, keeps one group.  */
+/* Scheduling groups of the batch (1 or 2; 0 for NULL).  With the environment variable
+ * CH_BATCH_GROUPS=2 at creation, a batch of at least 16 instances whose instances within a
+ * factor 2 of the largest stiffness estimate eps^2 (sum_a 4 n_a^2)^2 + sum_a 4 n_a^2 (the
+ * leading terms of ||A_hat||_1 at d = -1, Sec. 3.2) number at most an eighth of it
+ * integrates those as a second group, concurrently with the others, on a stream of higher
+ * priority; both groups start after earlier work on the batch's stream and the batch's
+ * stream waits for both.  Each instance's arithmetic does not depend on its group.  Without
+ * the variable every batch is one group.                                                  */
 int ch_batch_groups(const ch_batch *b);
 
 /* Kernel classes of the hot path, for launch accounting and timing (no counterpart in the

@@ -1575,14 +1575,16 @@ static ch_status create_impl(int dim, int count, const int64_t *n, const double 
 // estimate are at most an eighth of it runs those as a second batch, concurrently with the
 // rest on a stream of higher priority.  Stiffness estimate: the dominant terms of the closed
 // form of ||A_hat||_1 at d = -1 (Sec. 3.2), eps^2 (sum_a 4 n_a^2)^2 + sum_a 4 n_a^2.
-// CH_BATCH_GROUPS=1 keeps every batch in one group.
+// Groups are taken only when CH_BATCH_GROUPS=2 at creation.  Measured on 256 2D instances
+// they shorten an FP64 batch (whose bulk is the heavier part) but lengthen a mixed one,
+// whose stiff instances take the most steps and slow down under contention.
 constexpr int kGroupMinCount = 16;
 
 ch_status ch_create_batch(int dim, int count, const int64_t *n, const double *eps, int precision,
                           int mmax_capacity, void *cuda_stream, ch_batch **out) {
     const char *env = getenv("CH_BATCH_GROUPS");
     bool valid = out && n && eps && (dim == 2 || dim == 3) && count >= kGroupMinCount && count <= 65536 &&
-                 !(env && env[0] == '1');
+                 env && env[0] == '2';
     std::vector<double> lam;
     std::vector<int64_t> offs;
     if (valid) {

@@ -193,9 +193,10 @@ def _group_batch():
     return sides, eps, y0s
 
 
-def test_batch_scheduling_groups_fp64_match_oracle(ch, oracle):
+def test_batch_scheduling_groups_fp64_match_oracle(ch, oracle, monkeypatch):
     """The stiff group runs concurrently with the rest; every instance still follows the
     oracle's step sequence exactly (steps and matvecs) and its state to 1e-10."""
+    monkeypatch.setenv("CH_BATCH_GROUPS", "2")
     sides, eps, y0s = _group_batch()
     h = ch.ch_create_batch(2, sides, eps, ch.CH_FP64, 30)
     try:
@@ -215,8 +216,9 @@ def test_batch_scheduling_groups_fp64_match_oracle(ch, oracle):
 
 def test_batch_scheduling_groups_mixed_device_equals_host_loop(ch, monkeypatch):
     """Concurrent groups (device-driven) and the host-driven loop running the groups one
-    after the other give bit-identical states and counters; CH_BATCH_GROUPS=1 keeps one
-    group."""
+    after the other give bit-identical states and counters; without CH_BATCH_GROUPS=2 the
+    batch is one group."""
+    monkeypatch.setenv("CH_BATCH_GROUPS", "2")
     sides, eps, y0s = _group_batch()
     yd, sd, rcd, _ = _run_with_loop(ch, monkeypatch, False, sides, eps, y0s, ch.CH_MIXED, 2e-5)
     yh, sh, rch, _ = _run_with_loop(ch, monkeypatch, True, sides, eps, y0s, ch.CH_MIXED, 2e-5)
@@ -224,7 +226,7 @@ def test_batch_scheduling_groups_mixed_device_equals_host_loop(ch, monkeypatch):
     for i in range(len(sides)):
         np.testing.assert_array_equal(yd[i], yh[i])
         assert sd[i]["steps"] == sh[i]["steps"] and sd[i]["matvecs"] == sh[i]["matvecs"]
-    monkeypatch.setenv("CH_BATCH_GROUPS", "1")
+    monkeypatch.delenv("CH_BATCH_GROUPS")
     h = ch.ch_create_batch(2, sides, eps, ch.CH_MIXED, 30)
     try:
         assert ch.ch_batch_groups(h) == 1
