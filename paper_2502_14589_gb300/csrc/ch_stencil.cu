@@ -932,7 +932,7 @@ k_arnoldi_gmgs(Geom g, float *__restrict__ slot0, float *__restrict__ V, int64_t
     } else {
         // Larger grids: stage 2 runs here, tile by tile (two groups per thread), and each
         // tile's w and v_j meet every basis column while still on chip, so w is written once
-        // and neither it nor v_j is read again in this round (v_j serves as column j too).
+        // and neither it nor v_j is read again in round A (v_j serves as column j too).
         // Per-thread sums cover one tile and one column chunk; they are added across the
         // warp by a transposing shuffle tree and accumulated in the warp's 64 pair slots in
         // shared memory (slot k - 1: W_k . w, slot 32 + i - 1: W_i . W_j).
